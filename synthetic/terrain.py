@@ -1,0 +1,135 @@
+"""Seeded synthetic terrain shaped like the paper's scenes (Sec. VII-A uses procedurally
+generated mountains and forests and real LiDAR maps; neither is available here).
+
+Recipes (all elevations in metres, maps row-major ``[ny][nx]`` with x fastest, NaN = unknown):
+
+* ``bumpy_plane``: tilted plane tan(U[0, 15 deg]) * (cos a * x + sin a * y), a ~ U[0, 2 pi),
+  plus 8 Gaussian bumps (amplitude U[-0.5, 0.5] m, sigma U[0.3, 1.5] m, centres uniform
+  over the map) plus N(0, 0.01 m) noise.  Small map: 100 x 100 at 0.1 m.
+* ``fractal_steps_nan``: 6-octave value noise (base wavelength 8 m, lacunarity 2,
+  persistence 0.5, scaled to a peak |z| of 0.8 m), 3 step edges along random lines
+  (+U[0.05, 0.3] m on one side) and NaN discs of radius U[0.1, 0.5] m added until 5 %
+  of the cells are unknown.  Full local map: 400 x 400 at 0.05 m.
+* ``fractal_world``: the same recipe on a larger world, from which rolling windows are cut.
+* ``random_poses``: x, y uniform inside the map inset by a margin, yaw uniform [0, 2 pi).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def tilted_plane(nx, ny, res, alpha, beta, gamma, origin=(0, 0)):
+    """z = alpha * x + beta * y + gamma at the cell centres ((o + c + 1/2) * res)."""
+    oi, oj = origin
+    x = (oi + np.arange(nx) + 0.5) * res
+    y = (oj + np.arange(ny) + 0.5) * res
+    return (alpha * x[None, :] + beta * y[:, None] + gamma).astype(np.float64)
+
+
+def bumpy_plane(seed, nx=100, ny=100, res=0.1, n_bumps=8, noise=0.01, dtype=np.float32):
+    rng = np.random.default_rng(seed)
+    slope = np.tan(np.deg2rad(rng.uniform(0.0, 15.0)))
+    az = rng.uniform(0.0, 2 * np.pi)
+    x = (np.arange(nx) + 0.5) * res
+    y = (np.arange(ny) + 0.5) * res
+    X, Y = np.meshgrid(x, y)
+    z = slope * (np.cos(az) * X + np.sin(az) * Y)
+    w, h = nx * res, ny * res
+    for _ in range(n_bumps):
+        amp = rng.uniform(-0.5, 0.5)
+        sig = rng.uniform(0.3, 1.5)
+        cx, cy = rng.uniform(0, w), rng.uniform(0, h)
+        z += amp * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2 * sig * sig))
+    z += rng.normal(0.0, noise, size=z.shape)
+    return z.astype(dtype)
+
+
+def _value_noise(rng, nx, ny, res, wavelength):
+    """One octave of value noise: random lattice values with smoothstep interpolation."""
+    gx = int(np.ceil(nx * res / wavelength)) + 2
+    gy = int(np.ceil(ny * res / wavelength)) + 2
+    lat = rng.uniform(-1.0, 1.0, size=(gy, gx))
+    u = (np.arange(nx) + 0.5) * res / wavelength
+    v = (np.arange(ny) + 0.5) * res / wavelength
+    i0 = np.floor(u).astype(np.int64)
+    j0 = np.floor(v).astype(np.int64)
+    fu = u - i0
+    fv = v - j0
+    su = fu * fu * (3 - 2 * fu)
+    sv = fv * fv * (3 - 2 * fv)
+    a = lat[j0][:, i0]
+    b = lat[j0][:, i0 + 1]
+    c = lat[j0 + 1][:, i0]
+    d = lat[j0 + 1][:, i0 + 1]
+    top = a + (b - a) * su[None, :]
+    bot = c + (d - c) * su[None, :]
+    return top + (bot - top) * sv[:, None]
+
+
+def _fractal(rng, nx, ny, res, octaves=6, base=8.0, lacunarity=2.0, persistence=0.5, peak=0.8):
+    z = np.zeros((ny, nx))
+    amp, wl = 1.0, base
+    for _ in range(octaves):
+        z += amp * _value_noise(rng, nx, ny, res, wl)
+        amp *= persistence
+        wl /= lacunarity
+    z *= peak / np.max(np.abs(z))
+    return z
+
+
+def _steps(rng, z, res, n_steps=3):
+    ny, nx = z.shape
+    X, Y = np.meshgrid((np.arange(nx) + 0.5) * res, (np.arange(ny) + 0.5) * res)
+    for _ in range(n_steps):
+        px, py = rng.uniform(0, nx * res), rng.uniform(0, ny * res)
+        ang = rng.uniform(0, 2 * np.pi)
+        side = (X - px) * np.sin(ang) - (Y - py) * np.cos(ang) > 0
+        z = z + np.where(side, rng.uniform(0.05, 0.3), 0.0)
+    return z
+
+
+def _nan_discs(rng, z, res, frac=0.05):
+    ny, nx = z.shape
+    mask = np.zeros_like(z, dtype=bool)
+    target = frac * nx * ny
+    while mask.sum() < target:
+        r = rng.uniform(0.1, 0.5) / res
+        cx, cy = rng.uniform(0, nx), rng.uniform(0, ny)
+        x0, x1 = max(0, int(cx - r) - 1), min(nx, int(cx + r) + 2)
+        y0, y1 = max(0, int(cy - r) - 1), min(ny, int(cy + r) + 2)
+        yy, xx = np.mgrid[y0:y1, x0:x1]
+        mask[y0:y1, x0:x1] |= (xx + 0.5 - cx) ** 2 + (yy + 0.5 - cy) ** 2 <= r * r
+    z = z.copy()
+    z[mask] = np.nan
+    return z
+
+
+def fractal_steps_nan(seed, nx=400, ny=400, res=0.05, nan_frac=0.05, dtype=np.float32):
+    rng = np.random.default_rng(seed)
+    z = _fractal(rng, nx, ny, res)
+    z = _steps(rng, z, res)
+    if nan_frac > 0:
+        z = _nan_discs(rng, z, res, nan_frac)
+    return z.astype(dtype)
+
+
+def fractal_world(seed, n=2000, res=0.05, nan_frac=0.05, dtype=np.float32):
+    """A large world (n x n cells) from which robot-centric windows are cut."""
+    return fractal_steps_nan(seed, n, n, res, nan_frac, dtype)
+
+
+def shift_sequence(seed, n_shifts=50, step=10):
+    """Shifts of round(step * (cos phi, sin phi)) cells, phi ~ U[0, 2 pi)."""
+    rng = np.random.default_rng(seed)
+    phi = rng.uniform(0, 2 * np.pi, size=n_shifts)
+    return [(int(np.rint(step * np.cos(p))), int(np.rint(step * np.sin(p)))) for p in phi]
+
+
+def random_poses(seed, n, nx, ny, res, margin_cells, origin=(0, 0), dtype=np.float32):
+    """Poses [n, 3] = (x, y, yaw) in world metres, inset by margin_cells from the window edge."""
+    rng = np.random.default_rng(seed)
+    oi, oj = origin
+    x = (oi + rng.uniform(margin_cells, nx - margin_cells, size=n)) * res
+    y = (oj + rng.uniform(margin_cells, ny - margin_cells, size=n)) * res
+    th = rng.uniform(0.0, 2 * np.pi, size=n)
+    return np.stack([x, y, th], axis=1).astype(dtype)
