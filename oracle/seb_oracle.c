@@ -12,7 +12,7 @@
  *   1. the footprint: every integer cell offset (di, dj) whose coordinates in the body
  *      frame, (u, v) = R(-theta)(di, dj) in cell units, lie in the vehicle footprint
  *      (Algorithm 1, FindEllipticalPoints).  Rectangle: |u| <= a + 1e-6 and |v| <= b + 1e-6
- *      with a = length / (2 res), b = width / (2 res).  Ellipse: (u/a)^2 + (v/b)^2 <= 1 + 1e-9.
+ *      with a = length / (2 res), b = width / (2 res).  Ellipse: (u/a)^2 + (v/b)^2 <= 1 + 1e-6.
  *      Bins k >= n_yaw/2 use theta_{k - n_yaw/2}: the footprint is centrally symmetric, so
  *      the set at theta + pi is by definition the set at theta.
  *   2. the known points among them (inside the window and not NaN), as world points
@@ -73,7 +73,7 @@ static int inside_footprint(const orc_params* P, double theta, int di, int dj) {
   double u = c * di + s * dj;
   double v = -s * di + c * dj;
   if (P->shape == 0) return fabs(u) <= a + 1e-6 && fabs(v) <= b + 1e-6;
-  return (u / a) * (u / a) + (v / b) * (v / b) <= 1.0 + 1e-9;
+  return (u / a) * (u / a) + (v / b) * (v / b) <= 1.0 + 1e-6;
 }
 
 static double table_theta(const orc_params* P, int k) {

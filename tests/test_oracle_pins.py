@@ -73,7 +73,7 @@ def test_footprint_ellipse_rows():
     p = P(nx=5, ny=5, n_yaw=4, res=0.05, length=0.9, width=0.6, shape="ellipse")
     a, b = 9.0, 6.0
     fp = oracle.footprint(p, 0)
-    # per row dj the columns form |di| <= a sqrt(1 - (dj/b)^2) (up to the 1e-9 tolerance)
+    # per row dj the columns form |di| <= a sqrt(1 - (dj/b)^2) (up to the 1e-6 tolerance)
     want = sum(2 * int(math.floor(a * math.sqrt(max(0.0, 1 - (dj / b) ** 2)) + 1e-7)) + 1
                for dj in range(-6, 7))
     assert len(fp) == want
