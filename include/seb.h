@@ -1,0 +1,207 @@
+/*
+ * libseb: SE(2)-grid traversability assessment on sm_103a (SEB-Naver, arXiv 2503.02412).
+ *
+ * For every cell (c, r) of a robot-centric elevation window and every yaw bin k of n_yaw
+ * (theta_k = 2 pi k / n_yaw), the library gathers the elevation cells under the yaw-rotated
+ * vehicle footprint, fits their 3x3 covariance, takes the eigenvector of the smallest
+ * eigenvalue as the terrain normal z_b, builds the body frame of Eqs. 2-3 and scores risk
+ * with the curvature and the separate fore-aft / lateral tilt limits of Algorithm 1
+ * (Sec. V-B).  The window is a rolling map (Sec. V-A, Eq. (pm)): a move recomputes only
+ * the cells whose footprint touches cells that entered or left the window.
+ *
+ * Conventions shared by every entry point:
+ *   - elevation: row-major [ny][nx], x fastest, NaN = unknown; cell (c, r) has its centre
+ *     at world ((o_i + c + 1/2) res, (o_j + r + 1/2) res), (o_i, o_j) the integer grid index
+ *     of the window origin (Eq. (pm)).  Cells outside the window are unknown.
+ *   - outputs: SoA float32 out[ch][k][r][c], ch = z, pitch, roll, roughness, risk, plus
+ *     uint8 flags[k][r][c].  In the map's own buffers r and c are ring-indexed:
+ *     physical = (logical + ring offset) mod n (see seb_view).
+ *   - z = height of the fitted plane at the cell centre (m); pitch = asin(b3^T x_b),
+ *     roll = asin(b3^T y_b) (rad, signed; Algorithm 1 uses their magnitudes);
+ *     roughness = lambda_min / trace(Cov) (the curvature kappa_ter of Algorithm 1);
+ *     risk in [0, 1], 1 = obstacle.
+ *   - memory: every device buffer is owned by the caller.  The library never allocates
+ *     device memory and never synchronises, except where an entry point says so.
+ *   - streams: each call enqueues on the map's stream (seb_map_set_stream), or on the
+ *     stream argument for the map-free calls; NULL is the legacy default stream.
+ *   - errors: every call returns SEB_OK (0) or a negative SEB_ERR_* code and records a
+ *     message retrievable with seb_last_error.  Kernels never trap: device-side problems
+ *     set an error word that seb_map_check reads.
+ */
+#ifndef SEB_H_
+#define SEB_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define SEB_OK 0
+#define SEB_ERR_INVALID_ARG (-1)  /* NULL pointer, non-positive size, bad enum */
+#define SEB_ERR_BAD_SHAPE (-2)    /* n_yaw odd, footprint too large for the tables */
+#define SEB_ERR_CUDA (-3)         /* a CUDA runtime call failed */
+#define SEB_ERR_TIMEOUT (-4)      /* a bounded host wait ran out */
+#define SEB_ERR_DEVICE_FAULT (-5) /* a kernel raised the device error word */
+#define SEB_ERR_WORKSPACE (-6)    /* workspace too small or misaligned */
+
+/* Footprint shapes (Algorithm 1 uses an ellipse; the rectangle is the vehicle outline). */
+#define SEB_RECT 0
+#define SEB_ELLIPSE 1
+
+/* Elevation storage types. */
+#define SEB_F32 0
+#define SEB_BF16 1
+#define SEB_F16 2
+
+/* Moment accumulation. */
+#define SEB_PLAIN_F32 0   /* FP32 sums about the footprint's reference height */
+#define SEB_COMPENSATED 1 /* FP32 Neumaier-compensated sums about the same reference */
+
+/* Output flags. */
+#define SEB_FLAG_UNKNOWN 1    /* fewer than n_min known footprint cells */
+#define SEB_FLAG_OBSTACLE 2   /* risk == 1 (an explicit obstacle, Algorithm 1) */
+#define SEB_FLAG_DEGENERATE 4 /* normal undefined: eigen-gap ~ 0, n_z <= 1e-6 or yaw || normal */
+#define SEB_FLAG_FP64 8       /* eigen-solve redone in FP64 (small relative eigen-gap) */
+
+#define SEB_N_CH 5 /* z, pitch, roll, roughness, risk */
+
+typedef struct CUstream_st* seb_stream_t; /* the same type as cudaStream_t */
+typedef struct seb_map seb_map;
+
+/*
+ * Assessment parameters (Algorithm 1's inputs: footprint (e_x, e_y), w_r, kappa_max,
+ * phi_x_max, phi_y_max).  Footprint membership of an integer cell offset (di, dj) at yaw
+ * theta, with (u, v) = R(-theta)(di, dj) in cell units, a = length / (2 res),
+ * b = width / (2 res): rectangle |u| <= a + 1e-6 and |v| <= b + 1e-6; ellipse
+ * (u/a)^2 + (v/b)^2 <= 1 + 1e-6.  Bins k and k + n_yaw/2 share one footprint.
+ */
+typedef struct {
+  int32_t nx, ny;     /* window size in cells (>= 1) */
+  int32_t n_yaw;      /* yaw bins, even, 2..256 */
+  float res;          /* cell size (m) */
+  int32_t shape;      /* SEB_RECT | SEB_ELLIPSE */
+  float length;       /* footprint extent along the heading (m) */
+  float width;        /* footprint extent across the heading (m) */
+  float kappa_max;    /* roughness limit (default 0.1) */
+  float phi_x_max;    /* fore-aft tilt limit, rad (default 0.52, Sec. VII-B) */
+  float phi_y_max;    /* lateral tilt limit, rad (default 0.52, Sec. VII-B) */
+  float w[3];         /* risk weights for (kappa, |pitch|, |roll|) ratios (default 1/3 each) */
+  int32_t n_min;      /* minimum known footprint cells; 0 = max(3, ceil(N_k / 2)) per bin */
+  int32_t elev_dtype; /* SEB_F32 | SEB_BF16 | SEB_F16 */
+  int32_t precision;  /* SEB_PLAIN_F32 | SEB_COMPENSATED */
+  float gap_fp64;     /* relative eigen-gap below which the eigen-solve is redone in FP64 */
+} seb_params;
+
+/* Device pointers into a map's workspace, valid until the next update/shift/destroy. */
+typedef struct {
+  float* out;         /* [SEB_N_CH][n_yaw][ny][nx], ring-indexed */
+  uint8_t* flags;     /* [n_yaw][ny][nx], ring-indexed */
+  int32_t ring_x;     /* physical column = (logical + ring_x) mod nx */
+  int32_t ring_y;     /* physical row = (logical + ring_y) mod ny */
+  int64_t origin_i;   /* grid index of the window origin (Eq. (pm)) */
+  int64_t origin_j;
+  size_t out_offset;  /* byte offsets of out / flags from the workspace base */
+  size_t flags_offset;
+} seb_view;
+
+/* Fills p with the defaults above (c1 geometry: 100 x 100 at 0.1 m, 36 bins, 0.6 x 0.4 m). */
+void seb_params_default(seb_params* p);
+
+/* Message for a status code (static storage). */
+const char* seb_status_string(int status);
+
+/* Last error message of the calling thread, or of a map when m is not NULL. */
+const char* seb_last_error(const seb_map* m);
+
+/*
+ * Footprint table of yaw bin k (host only, no GPU needed): writes up to cap offsets
+ * (di, dj) in row-run order (dj ascending, di ascending) and returns the count, or a
+ * negative status.  Used to check the tables against an independent enumeration.
+ */
+int seb_footprint_table(const seb_params* p, int32_t k, int32_t* di, int32_t* dj, int32_t cap);
+
+/* Bytes of device workspace a map needs: the SoA outputs, the flags and a small control
+ * block (the device error word and counters). */
+size_t seb_workspace_bytes(const seb_params* p);
+
+/*
+ * Creates a map over caller-owned device workspace (>= seb_workspace_bytes, 256-byte
+ * aligned).  Builds the footprint tables on the host; allocates host memory only.
+ * Outputs are undefined until the first seb_map_update.
+ */
+int seb_map_create(const seb_params* p, void* workspace_dev, size_t bytes, seb_stream_t stream,
+                   seb_map** out);
+
+/* Frees the host handle.  The workspace stays the caller's. */
+int seb_map_destroy(seb_map* m);
+
+/* Sets the stream later calls enqueue on. */
+int seb_map_set_stream(seb_map* m, seb_stream_t stream);
+
+/*
+ * Full rebuild (Algorithm 1 for every SE(2) cell).  elev_dev: device [ny][nx] in the map's
+ * elev_dtype, logical order, at least 16-byte aligned; read only during the call's kernels.
+ * (origin_i, origin_j): grid index of the window origin.  Resets the ring offsets to 0.
+ */
+int seb_map_update(seb_map* m, const void* elev_dev, int64_t origin_i, int64_t origin_j);
+
+/*
+ * Rolling update (Sec. V-A): the window moves to (origin_i, origin_j); elev_dev holds the
+ * whole new window in logical order.  The ring offsets advance by the move, and only the
+ * cells whose footprint can see a cell that entered or left the window are recomputed:
+ * a band of |move| + reach cells on the entering side and of reach cells on the leaving
+ * side, per axis (reach = largest |offset| of any footprint along that axis).  Every
+ * other cell keeps its stored value, which is bit-identical to a full rebuild.  A move of
+ * at least the window size in either axis falls back to a full rebuild.
+ */
+int seb_map_shift(seb_map* m, const void* elev_dev, int64_t origin_i, int64_t origin_j);
+
+/* Pointers and ring offsets of the current outputs. */
+int seb_map_view(const seb_map* m, seb_view* v);
+
+/* Copies the outputs to caller buffers in logical order (undoing the ring):
+ * out_dev [SEB_N_CH][n_yaw][ny][nx] float32, flags_dev [n_yaw][ny][nx] (either may be NULL). */
+int seb_map_copy_out(const seb_map* m, float* out_dev, uint8_t* flags_dev);
+
+/*
+ * Synchronises the map's stream (bounded wait of timeout_ms; <= 0 waits without bound),
+ * reads the device error word and the counters, and clears them.  n_fp64 / n_degenerate
+ * (may be NULL) receive the number of eigen-solves redone in FP64 and of degenerate cells
+ * since the last check.  Returns SEB_ERR_DEVICE_FAULT if a kernel raised the error word.
+ */
+int seb_map_check(seb_map* m, int32_t timeout_ms, int64_t* n_fp64, int64_t* n_degenerate);
+
+/*
+ * Continuous-pose query (a differentiable form of the same assessment): for each pose
+ * (x, y, yaw) in world metres/radians, the yaw-0 footprint lattice {(di res, dj res)} is
+ * rotated by yaw and translated to (x, y); each lattice point takes the bilinear elevation
+ * of the four surrounding cell centres (unknown if any of them is NaN or outside the
+ * window); then covariance, normal, frame, outputs and risk follow Algorithm 1 as above,
+ * with z the fitted-plane height at (x, y).
+ *   poses_dev [n][3] float32; out_dev [n][SEB_N_CH] float32; flags_dev [n] uint8;
+ *   saved_dev [n][SEB_QUERY_SAVED] float32 or NULL: per-pose state the backward reuses.
+ */
+#define SEB_QUERY_SAVED 16
+int seb_query_poses(const seb_params* p, const void* elev_dev, int64_t origin_i, int64_t origin_j,
+                    const float* poses_dev, int64_t n, float* out_dev, uint8_t* flags_dev,
+                    float* saved_dev, seb_stream_t stream);
+
+/*
+ * Hand-written adjoint of seb_query_poses: grad_pose[i] = sum_ch grad_out[i][ch] *
+ * d out[i][ch] / d pose[i] for ch in (z, pitch, roll, risk) (grad_out [n][4]).  The set of
+ * known lattice points is held fixed; the risk gradient is 0 on the clamped (risk = 1)
+ * branches and sign(0) = 0 at |.| kinks.  saved_dev may be NULL (recomputed).
+ */
+int seb_query_poses_backward(const seb_params* p, const void* elev_dev, int64_t origin_i,
+                             int64_t origin_j, const float* poses_dev, const float* saved_dev,
+                             const float* grad_out_dev, float* grad_pose_dev, int64_t n,
+                             seb_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEB_H_ */

@@ -1,0 +1,9 @@
+"""GB300-native SE(2)-grid traversability assessment (SEB-Naver, arXiv 2503.02412, Sec. V).
+
+The compute path is libseb.so (hand-written CUDA for sm_103a behind a C ABI, include/seb.h);
+this package only marshals torch tensors and streams into it.
+"""
+from . import abi  # noqa: F401
+from .maps import CHANNELS, SebMap, SebParams  # noqa: F401
+
+__all__ = ["abi", "SebMap", "SebParams", "CHANNELS"]

@@ -1,0 +1,222 @@
+"""ctypes binding of libseb's C ABI (include/seb.h), one Python function per C entry point,
+same names.  Argument marshalling only: every step of the assessment runs in libseb's CUDA
+kernels.  Pointers are plain integers (device addresses); streams are raw cudaStream_t
+handles.  A missing libseb.so raises at first use: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libseb.so")
+
+SEB_OK = 0
+SEB_ERR_INVALID_ARG = -1
+SEB_ERR_BAD_SHAPE = -2
+SEB_ERR_CUDA = -3
+SEB_ERR_TIMEOUT = -4
+SEB_ERR_DEVICE_FAULT = -5
+SEB_ERR_WORKSPACE = -6
+
+SEB_RECT, SEB_ELLIPSE = 0, 1
+SEB_F32, SEB_BF16, SEB_F16 = 0, 1, 2
+SEB_PLAIN_F32, SEB_COMPENSATED = 0, 1
+SEB_FLAG_UNKNOWN, SEB_FLAG_OBSTACLE, SEB_FLAG_DEGENERATE, SEB_FLAG_FP64 = 1, 2, 4, 8
+SEB_N_CH = 5
+SEB_QUERY_SAVED = 16
+
+# Every extern "C" symbol declared in include/seb.h.
+EXPORTS = (
+    "seb_params_default",
+    "seb_status_string",
+    "seb_last_error",
+    "seb_footprint_table",
+    "seb_workspace_bytes",
+    "seb_map_create",
+    "seb_map_destroy",
+    "seb_map_set_stream",
+    "seb_map_update",
+    "seb_map_shift",
+    "seb_map_view",
+    "seb_map_copy_out",
+    "seb_map_check",
+    "seb_query_poses",
+    "seb_query_poses_backward",
+)
+
+
+class SebError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libseb status {status}: {msg}")
+        self.status = status
+
+
+class seb_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32),
+        ("ny", ctypes.c_int32),
+        ("n_yaw", ctypes.c_int32),
+        ("res", ctypes.c_float),
+        ("shape", ctypes.c_int32),
+        ("length", ctypes.c_float),
+        ("width", ctypes.c_float),
+        ("kappa_max", ctypes.c_float),
+        ("phi_x_max", ctypes.c_float),
+        ("phi_y_max", ctypes.c_float),
+        ("w", ctypes.c_float * 3),
+        ("n_min", ctypes.c_int32),
+        ("elev_dtype", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("gap_fp64", ctypes.c_float),
+    ]
+
+
+class seb_view(ctypes.Structure):
+    _fields_ = [
+        ("out", ctypes.c_void_p),
+        ("flags", ctypes.c_void_p),
+        ("ring_x", ctypes.c_int32),
+        ("ring_y", ctypes.c_int32),
+        ("origin_i", ctypes.c_int64),
+        ("origin_j", ctypes.c_int64),
+        ("out_offset", ctypes.c_size_t),
+        ("flags_offset", ctypes.c_size_t),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load():
+    """Loads libseb.so (built in-tree by paper_2503_02412_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with `python -m paper_2503_02412_gb300.build` "
+                "(there is no CPU fallback)")
+        lib = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER(seb_params)
+        vp = ctypes.c_void_p
+        i32, i64, sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        sig = {
+            "seb_params_default": (None, [P]),
+            "seb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "seb_last_error": (ctypes.c_char_p, [vp]),
+            "seb_footprint_table": (ctypes.c_int, [P, i32, i32p, i32p, i32]),
+            "seb_workspace_bytes": (sz, [P]),
+            "seb_map_create": (ctypes.c_int, [P, vp, sz, vp, ctypes.POINTER(vp)]),
+            "seb_map_destroy": (ctypes.c_int, [vp]),
+            "seb_map_set_stream": (ctypes.c_int, [vp, vp]),
+            "seb_map_update": (ctypes.c_int, [vp, vp, i64, i64]),
+            "seb_map_shift": (ctypes.c_int, [vp, vp, i64, i64]),
+            "seb_map_view": (ctypes.c_int, [vp, ctypes.POINTER(seb_view)]),
+            "seb_map_copy_out": (ctypes.c_int, [vp, vp, vp]),
+            "seb_map_check": (ctypes.c_int, [vp, i32, i64p, i64p]),
+            "seb_query_poses": (ctypes.c_int, [P, vp, i64, i64, vp, i64, vp, vp, vp, vp]),
+            "seb_query_poses_backward": (ctypes.c_int, [P, vp, i64, i64, vp, vp, vp, vp, i64, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc, handle=None):
+    if rc != SEB_OK:
+        lib = load()
+        msg = lib.seb_last_error(handle)
+        raise SebError(rc, (msg or b"").decode() or lib.seb_status_string(rc).decode())
+    return rc
+
+
+# ---------------------------------------------------------------- one wrapper per entry point
+
+
+def seb_params_default() -> seb_params:
+    p = seb_params()
+    load().seb_params_default(ctypes.byref(p))
+    return p
+
+
+def seb_status_string(status: int) -> str:
+    return load().seb_status_string(status).decode()
+
+
+def seb_last_error(handle=None) -> str:
+    return (load().seb_last_error(handle) or b"").decode()
+
+
+def seb_footprint_table(p: seb_params, k: int):
+    """Offsets of yaw bin k as a list of (di, dj) in row-run order (host only)."""
+    lib = load()
+    n = lib.seb_footprint_table(ctypes.byref(p), k, None, None, 0)
+    _check(n if n < 0 else 0)
+    di = (ctypes.c_int32 * max(n, 1))()
+    dj = (ctypes.c_int32 * max(n, 1))()
+    lib.seb_footprint_table(ctypes.byref(p), k, di, dj, n)
+    return [(di[i], dj[i]) for i in range(n)]
+
+
+def seb_workspace_bytes(p: seb_params) -> int:
+    return int(load().seb_workspace_bytes(ctypes.byref(p)))
+
+
+def seb_map_create(p: seb_params, workspace_ptr: int, nbytes: int, stream: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(load().seb_map_create(ctypes.byref(p), workspace_ptr, nbytes, stream, ctypes.byref(h)))
+    return h.value
+
+
+def seb_map_destroy(handle: int) -> None:
+    _check(load().seb_map_destroy(handle))
+
+
+def seb_map_set_stream(handle: int, stream: int) -> None:
+    _check(load().seb_map_set_stream(handle, stream), handle)
+
+
+def seb_map_update(handle: int, elev_ptr: int, origin_i: int, origin_j: int) -> None:
+    _check(load().seb_map_update(handle, elev_ptr, origin_i, origin_j), handle)
+
+
+def seb_map_shift(handle: int, elev_ptr: int, origin_i: int, origin_j: int) -> None:
+    _check(load().seb_map_shift(handle, elev_ptr, origin_i, origin_j), handle)
+
+
+def seb_map_view(handle: int) -> seb_view:
+    v = seb_view()
+    _check(load().seb_map_view(handle, ctypes.byref(v)), handle)
+    return v
+
+
+def seb_map_copy_out(handle: int, out_ptr: int, flags_ptr: int) -> None:
+    _check(load().seb_map_copy_out(handle, out_ptr, flags_ptr), handle)
+
+
+def seb_map_check(handle: int, timeout_ms: int = 10000):
+    """Returns (n_fp64, n_degenerate); raises SebError on a device error or timeout."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().seb_map_check(handle, timeout_ms, ctypes.byref(a), ctypes.byref(b)), handle)
+    return a.value, b.value
+
+
+def seb_query_poses(p: seb_params, elev_ptr, origin_i, origin_j, poses_ptr, n, out_ptr, flags_ptr,
+                    saved_ptr, stream=0) -> None:
+    _check(load().seb_query_poses(ctypes.byref(p), elev_ptr, origin_i, origin_j, poses_ptr, n, out_ptr,
+                                  flags_ptr, saved_ptr, stream))
+
+
+def seb_query_poses_backward(p: seb_params, elev_ptr, origin_i, origin_j, poses_ptr, saved_ptr,
+                             grad_out_ptr, grad_pose_ptr, n, stream=0) -> None:
+    _check(load().seb_query_poses_backward(ctypes.byref(p), elev_ptr, origin_i, origin_j, poses_ptr,
+                                           saved_ptr, grad_out_ptr, grad_pose_ptr, n, stream))

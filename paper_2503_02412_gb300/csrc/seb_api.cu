@@ -1,0 +1,308 @@
+// C ABI of libseb (declared in include/seb.h): map lifetime, full rebuild, rolling shift
+// (Sec. V-A: the window follows the robot, Eq. (pm); cells that leave become unknown),
+// views, copies and error reporting.  Host-side logic only; kernels live in the other
+// translation units.
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <chrono>
+#include <new>
+#include <thread>
+
+#include "seb_internal.h"
+
+struct seb_map {
+  seb_params p;
+  seb::Tables T;
+  int32_t total_runs;
+  uint8_t* ws;
+  size_t ws_bytes;
+  cudaStream_t stream;
+  float* out;
+  uint8_t* flags;
+  seb::Control* ctl;
+  int32_t ring_x, ring_y;
+  int64_t oi, oj;
+  bool valid;
+  char err[256];
+};
+
+namespace seb {
+
+static thread_local char g_err[256] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+static int cuda_fail(seb_map* m, cudaError_t e, const char* where) {
+  set_error("%s: %s", where, cudaGetErrorString(e));
+  if (m) snprintf(m->err, sizeof(m->err), "%s", g_err);
+  return SEB_ERR_CUDA;
+}
+
+static int fail(seb_map* m, int code, const char* msg) {
+  set_error("%s", msg);
+  if (m) snprintf(m->err, sizeof(m->err), "%s", msg);
+  return code;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static Launch base_launch(const seb_map* m, const void* elev) {
+  Launch L;
+  memset(&L, 0, sizeof(L));
+  L.elev = elev;
+  L.nx = m->p.nx;
+  L.ny = m->p.ny;
+  L.ring_x = m->ring_x;
+  L.ring_y = m->ring_y;
+  L.out = m->out;
+  L.flags = m->flags;
+  L.plane = (int64_t)m->p.nx * m->p.ny;
+  L.n_yaw = m->p.n_yaw;
+  L.res = m->p.res;
+  L.kappa_max = m->p.kappa_max;
+  L.phi_x_max = m->p.phi_x_max;
+  L.phi_y_max = m->p.phi_y_max;
+  L.w0 = m->p.w[0];
+  L.w1 = m->p.w[1];
+  L.w2 = m->p.w[2];
+  L.gap_fp64 = m->p.gap_fp64;
+  int sw = kTileW + 2 * m->T.rx;
+  if ((sw & 1) == 0) ++sw;  // odd row pitch: the 4 rows a warp touches hit distinct banks
+  L.sw = sw;
+  L.sh = kTileH + 2 * m->T.ry;
+  L.err = &m->ctl->err;
+  L.counters = &m->ctl->n_fp64;
+  return L;
+}
+
+static void add_rect(Launch& L, int x0, int y0, int w, int h) {
+  if (w <= 0 || h <= 0) return;
+  const int i = L.n_rects++;
+  L.rects[i] = Rect{x0, y0, w, h};
+  L.tiles_x[i] = (w + kTileW - 1) / kTileW;
+  const int ty = (h + kTileH - 1) / kTileH;
+  L.tile_start[i + 1] = L.tile_start[i] + L.tiles_x[i] * ty;
+}
+
+static int check_elev(seb_map* m, const void* elev) {
+  if (!elev) return fail(m, SEB_ERR_INVALID_ARG, "elevation pointer is NULL");
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, elev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(m, e, "cudaPointerGetAttributes(elevation)");
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+    return fail(m, SEB_ERR_INVALID_ARG, "elevation must be device memory");
+  return SEB_OK;
+}
+
+}  // namespace seb
+
+using namespace seb;
+
+extern "C" {
+
+void seb_params_default(seb_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->nx = 100;
+  p->ny = 100;
+  p->n_yaw = 36;
+  p->res = 0.1f;
+  p->shape = SEB_RECT;
+  p->length = 0.6f;
+  p->width = 0.4f;
+  p->kappa_max = 0.1f;
+  p->phi_x_max = 0.52f;
+  p->phi_y_max = 0.52f;
+  p->w[0] = p->w[1] = p->w[2] = 1.0f / 3.0f;
+  p->n_min = 0;
+  p->elev_dtype = SEB_F32;
+  p->precision = SEB_PLAIN_F32;
+  p->gap_fp64 = 1e-6f;
+}
+
+const char* seb_status_string(int s) {
+  switch (s) {
+    case SEB_OK: return "ok";
+    case SEB_ERR_INVALID_ARG: return "invalid argument";
+    case SEB_ERR_BAD_SHAPE: return "unsupported shape";
+    case SEB_ERR_CUDA: return "CUDA error";
+    case SEB_ERR_TIMEOUT: return "timeout";
+    case SEB_ERR_DEVICE_FAULT: return "device error word set";
+    case SEB_ERR_WORKSPACE: return "workspace too small or misaligned";
+    default: return "unknown status";
+  }
+}
+
+const char* seb_last_error(const seb_map* m) { return m ? m->err : g_err; }
+
+size_t seb_workspace_bytes(const seb_params* p) {
+  if (!p || validate_params(*p) != SEB_OK) return 0;
+  return kControlBytes + align256(out_bytes(*p)) + align256(flags_bytes(*p));
+}
+
+int seb_map_create(const seb_params* p, void* ws, size_t bytes, seb_stream_t stream, seb_map** out) {
+  if (!p || !out) return fail(nullptr, SEB_ERR_INVALID_ARG, "params or out pointer is NULL");
+  *out = nullptr;
+  int rc = validate_params(*p);
+  if (rc) return fail(nullptr, rc, "invalid parameters");
+  if (!ws || ((uintptr_t)ws & 255)) return fail(nullptr, SEB_ERR_WORKSPACE, "workspace NULL or not 256-byte aligned");
+  if (bytes < seb_workspace_bytes(p)) return fail(nullptr, SEB_ERR_WORKSPACE, "workspace too small");
+  seb_map* m = new (std::nothrow) seb_map;
+  if (!m) return fail(nullptr, SEB_ERR_INVALID_ARG, "out of host memory");
+  memset(m, 0, sizeof(*m));
+  m->p = *p;
+  rc = build_tables(*p, &m->T, &m->total_runs);
+  if (rc) {
+    delete m;
+    return rc;
+  }
+  m->ws = (uint8_t*)ws;
+  m->ws_bytes = bytes;
+  m->stream = (cudaStream_t)stream;
+  m->ctl = (Control*)ws;
+  m->out = (float*)(m->ws + kControlBytes);
+  m->flags = m->ws + kControlBytes + align256(out_bytes(*p));
+  cudaError_t e = cudaMemsetAsync(m->ctl, 0, sizeof(Control), m->stream);
+  if (e != cudaSuccess) {
+    delete m;
+    return cuda_fail(nullptr, e, "cudaMemsetAsync(control)");
+  }
+  *out = m;
+  return SEB_OK;
+}
+
+int seb_map_destroy(seb_map* m) {
+  if (!m) return SEB_ERR_INVALID_ARG;
+  delete m;
+  return SEB_OK;
+}
+
+int seb_map_set_stream(seb_map* m, seb_stream_t s) {
+  if (!m) return fail(nullptr, SEB_ERR_INVALID_ARG, "map is NULL");
+  m->stream = (cudaStream_t)s;
+  return SEB_OK;
+}
+
+int seb_map_update(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
+  if (!m) return fail(nullptr, SEB_ERR_INVALID_ARG, "map is NULL");
+  int rc = check_elev(m, elev);
+  if (rc) return rc;
+  m->ring_x = m->ring_y = 0;
+  Launch L = base_launch(m, elev);
+  add_rect(L, 0, 0, m->p.nx, m->p.ny);
+  cudaError_t e = launch_assess(m->T, L, m->p.elev_dtype, m->p.precision, m->stream);
+  if (e != cudaSuccess) return cuda_fail(m, e, "assess launch");
+  m->oi = oi;
+  m->oj = oj;
+  m->valid = true;
+  return SEB_OK;
+}
+
+int seb_map_shift(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
+  if (!m) return fail(nullptr, SEB_ERR_INVALID_ARG, "map is NULL");
+  if (!m->valid) return seb_map_update(m, elev, oi, oj);
+  int rc = check_elev(m, elev);
+  if (rc) return rc;
+  const int64_t dx = oi - m->oi, dy = oj - m->oj;
+  const int nx = m->p.nx, ny = m->p.ny;
+  if (dx >= nx || -dx >= nx || dy >= ny || -dy >= ny) return seb_map_update(m, elev, oi, oj);
+  if (dx == 0 && dy == 0) return SEB_OK;
+  // Logical cell c of the new window is logical c + dx of the old one; the ring offset
+  // keeps every surviving cell at its physical address.
+  m->ring_x = (int32_t)(((m->ring_x + dx) % nx + nx) % nx);
+  m->ring_y = (int32_t)(((m->ring_y + dy) % ny + ny) % ny);
+  const int rx = m->T.rx, ry = m->T.ry;
+  // Column bands: cells that now see entering columns, and cells that used to see columns
+  // that left the window.
+  int left = 0, right = 0, top = 0, bottom = 0;
+  if (dx > 0) {
+    right = (int)dx + rx;
+    left = rx;
+  } else if (dx < 0) {
+    left = (int)(-dx) + rx;
+    right = rx;
+  }
+  if (dy > 0) {
+    bottom = (int)dy + ry;
+    top = ry;
+  } else if (dy < 0) {
+    top = (int)(-dy) + ry;
+    bottom = ry;
+  }
+  Launch L = base_launch(m, elev);
+  if (left + right >= nx || top + bottom >= ny) {
+    add_rect(L, 0, 0, nx, ny);
+  } else {
+    add_rect(L, 0, 0, left, ny);
+    add_rect(L, nx - right, 0, right, ny);
+    add_rect(L, left, 0, nx - left - right, top);
+    add_rect(L, left, ny - bottom, nx - left - right, bottom);
+  }
+  cudaError_t e = launch_assess(m->T, L, m->p.elev_dtype, m->p.precision, m->stream);
+  if (e != cudaSuccess) return cuda_fail(m, e, "assess launch (shift)");
+  m->oi = oi;
+  m->oj = oj;
+  return SEB_OK;
+}
+
+int seb_map_view(const seb_map* m, seb_view* v) {
+  if (!m || !v) return fail(nullptr, SEB_ERR_INVALID_ARG, "map or view is NULL");
+  v->out = m->out;
+  v->flags = m->flags;
+  v->ring_x = m->ring_x;
+  v->ring_y = m->ring_y;
+  v->origin_i = m->oi;
+  v->origin_j = m->oj;
+  v->out_offset = (size_t)((uint8_t*)m->out - m->ws);
+  v->flags_offset = (size_t)(m->flags - m->ws);
+  return SEB_OK;
+}
+
+int seb_map_copy_out(const seb_map* m, float* out_dev, uint8_t* flags_dev) {
+  if (!m) return fail(nullptr, SEB_ERR_INVALID_ARG, "map is NULL");
+  if (!out_dev && !flags_dev) return SEB_OK;
+  Launch L = base_launch(m, nullptr);
+  cudaError_t e = launch_copy_out(L, out_dev, flags_dev, m->stream);
+  if (e != cudaSuccess) return cuda_fail(const_cast<seb_map*>(m), e, "copy_out launch");
+  return SEB_OK;
+}
+
+int seb_map_check(seb_map* m, int32_t timeout_ms, int64_t* n_fp64, int64_t* n_degenerate) {
+  if (!m) return fail(nullptr, SEB_ERR_INVALID_ARG, "map is NULL");
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t q = cudaStreamQuery(m->stream);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) return cuda_fail(m, q, "cudaStreamQuery");
+    if (timeout_ms > 0 &&
+        std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(timeout_ms))
+      return fail(m, SEB_ERR_TIMEOUT, "stream did not finish within the timeout");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  Control c;
+  cudaError_t e = cudaMemcpyAsync(&c, m->ctl, sizeof(c), cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->ctl, 0, sizeof(Control), m->stream);
+  if (e != cudaSuccess) return cuda_fail(m, e, "reading the control block");
+  if (n_fp64) *n_fp64 = (int64_t)c.n_fp64;
+  if (n_degenerate) *n_degenerate = (int64_t)c.n_degenerate;
+  if (c.err) {
+    char msg[96];
+    snprintf(msg, sizeof(msg), "device error word 0x%x", c.err);
+    return fail(m, SEB_ERR_DEVICE_FAULT, msg);
+  }
+  return SEB_OK;
+}
+
+}  // extern "C"
