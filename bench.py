@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark of the SE(2)-grid traversability hot path on the full local map:
+400 x 400 cells at 0.05 m, 72 yaw bins, 0.9 x 0.6 m footprint, fractal terrain with steps and
+5 % unknown cells.  One step = a full rebuild of the map (11.52 M SE(2) cells) followed by 50
+rolling shifts of 10 cells in random directions, each recomputing only the affected bands.
+
+Prints one JSON line.  value = SE(2) cells assessed per second over the timed steps (cells
+actually recomputed: the rebuild plus every shift band), whole job over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores (a bounded random sample of the
+same workload's cells per step); under torchrun only rank 0 runs it.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX = NY = 400
+K = 72
+RES = 0.05
+LENGTH, WIDTH = 0.9, 0.6
+N_SHIFTS = 50
+WORLD = 1200
+WORKLOAD = "se2_map_400x400x72_rebuild_plus_50_shifts"
+
+# ncu DRAM traffic of one full-map rebuild launch (dram__bytes_read.sum + dram__bytes_write.sum),
+# valid only for the kernel source it was captured on (hash of the assess kernel's sources).
+NCU_TRAFFIC = {"sources_sha": "76ccfd40278794e3", "bytes": 22289664 + 206337280}
+
+
+def kernel_sources_sha():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2503_02412_gb300", "csrc")
+    for f in ("seb_assess.cu", "seb_device.cuh", "seb_internal.h"):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def workload(seed=1):
+    """World, window origins and shift sequence (identical on every rank: replicas)."""
+    from synthetic import fractal_world, shift_sequence
+
+    world = fractal_world(seed, WORLD, RES)
+    o = [(WORLD - NX) // 2, (WORLD - NY) // 2]
+    origins = [tuple(o)]
+    for dx, dy in shift_sequence(seed + 1, N_SHIFTS, 10):
+        o = [min(max(o[0] + dx, 0), WORLD - NX), min(max(o[1] + dy, 0), WORLD - NY)]
+        origins.append(tuple(o))
+    return world, origins
+
+
+def oracle_params():
+    import oracle
+
+    return oracle.OracleParams(nx=NX, ny=NY, n_yaw=K, res=RES, length=LENGTH, width=WIDTH)
+
+
+def cpu_baseline(world, origins, budget_s, rng_seed=0):
+    """Times the FP64 oracle on a bounded random sample of the rebuild's cells."""
+    import oracle
+
+    oracle.build()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    o = origins[0]
+    e = world[o[1]:o[1] + NY, o[0]:o[0] + NX].astype(np.float64)
+    rng = np.random.default_rng(rng_seed)
+    p = oracle_params()
+    n = 20000
+    while True:  # calibrate: grow the sample until it takes about budget_s
+        cells = np.stack([rng.integers(0, NX, n), rng.integers(0, NY, n), rng.integers(0, K, n)], 1).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.assess_cells(p, e, cells, o, n_threads=cores)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 4 or n >= 50_000_000:
+            break
+        n = int(n * min(8.0, max(2.0, budget_s / 4 / max(dt, 1e-3))))
+    return {"value": n / dt, "unit": "SE(2) cells/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} random (c, r, k) cells of the 400x400x72 rebuild, FP64 brute force, {dt:.2f} s"}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}", "--format=csv,noheader",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                smax.append(float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def flush_l2(buf):
+    buf.add_(1)  # writes 256 MB (> 129 MB L2)
+
+
+def run_reference(args):
+    rank, _, world_size = dist_env()
+    if rank != 0:
+        return
+    world, origins = workload()
+    per_step = max(1.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    cb = cpu_baseline(world, origins, per_step * 4)
+    import oracle
+
+    p = oracle_params()
+    o = origins[0]
+    e = world[o[1]:o[1] + NY, o[0]:o[0] + NX].astype(np.float64)
+    rng = np.random.default_rng(1)
+    n = int(cb["value"] * per_step)
+    cells = np.stack([rng.integers(0, NX, n), rng.integers(0, NY, n), rng.integers(0, K, n)], 1).astype(np.int32)
+    for _ in range(args.warmup):
+        oracle.assess_cells(p, e, cells[: max(1, n // 10)], o, n_threads=cb["cores"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.assess_cells(p, e, cells, o, n_threads=cb["cores"])
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt
+    line = {"impl": "reference", "metric": "SE(2) cells/s (400x400x72 map, rebuild + rolling shifts)",
+            "value": value, "unit": "SE(2) cells/s", "n_gpus": world_size, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_cells_per_step": n, "l2": "n/a (host)"},
+            "cpu_baseline": dict(cb, value=value,
+                                 sample=f"{n} random (c, r, k) cells per step of the 400x400x72 map, FP64 oracle"),
+            "e2e": {"value": value, "unit": "SE(2) cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, local_rank, world_size = dist_env()
+    import torch
+
+    if world_size > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    import paper_2503_02412_gb300 as seb
+    from paper_2503_02412_gb300 import abi
+
+    abi.load()  # fails loudly if the CUDA library is missing: no fallback
+    world_np, origins = workload()
+    world = torch.from_numpy(world_np).to(dev)
+    wins = [world[o[1]:o[1] + NY, o[0]:o[0] + NX].contiguous() for o in origins]
+    params = seb.SebParams(nx=NX, ny=NY, n_yaw=K, res=RES, length=LENGTH, width=WIDTH)
+    m = seb.SebMap(params, dev)
+    stream = torch.cuda.current_stream(dev)
+    l2buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def step(ev_rebuild=None):
+        if ev_rebuild is not None:
+            ev_rebuild[0].record(stream)
+        m.update(wins[0], origins[0])
+        if ev_rebuild is not None:
+            ev_rebuild[1].record(stream)
+        cells = m.view().last_cells
+        for w, o in zip(wins[1:], origins[1:]):
+            m.shift(w, o)
+            cells += m.view().last_cells
+        return cells
+
+    for _ in range(args.warmup):
+        step()
+    m.check()
+    torch.cuda.synchronize(dev)
+    if world_size > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local_rank)
+    total_ms = 0.0
+    rebuild_ms = []
+    cells_total = 0
+    launches = 0
+    for _ in range(args.steps):
+        flush_l2(l2buf)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        cells_total += step((ev[2], ev[3]))
+        ev[1].record(stream)
+        ev[1].synchronize()
+        total_ms += ev[0].elapsed_time(ev[1])
+        rebuild_ms.append(ev[2].elapsed_time(ev[3]))
+        launches += 1 + sum(1 for i in range(1, len(origins)) if origins[i] != origins[i - 1])
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    n64, ndeg = m.check()
+    if world_size > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    ms_per_step = total_ms / args.steps
+    value = cells_total * world_size / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (the full-map rebuild launch)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sizes = [len(abi.seb_footprint_table(params.c(), k)) for k in range(K // 2)]
+    flop = NX * NY * sum(9 * n + 200 for n in sizes)  # algorithmic FLOP per rebuild (yaw pairs)
+    rb = float(np.mean(rebuild_ms))
+    achieved = flop / (rb * 1e-3) / 1e12
+    peak = sms * 128 * 2 * 2070e6 / 1e12  # FP32 lanes x FMA x max SM clock
+    traffic = NCU_TRAFFIC["bytes"] if NCU_TRAFFIC["sources_sha"] == kernel_sources_sha() else None
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(seb, m, world_np, origins, args, dev)
+    line = {
+        "metric": "SE(2) cells/s (400x400x72 map: full rebuild + 50 rolling shifts per step)",
+        "value": value, "unit": "SE(2) cells/s", "n_gpus": world_size, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "n_yaw": K, "res_m": RES,
+                   "footprint_m": [LENGTH, WIDTH], "shifts_per_step": N_SHIFTS,
+                   "cells_per_step": cells_total // args.steps, "parallelism": f"replicas x{world_size}",
+                   "l2": "flushed before every timed step (256 MB write)"},
+        "rebuild_ms": rb, "rebuild_cells_per_s": NX * NY * K / (rb * 1e-3),
+        "shift_us_mean": (ms_per_step - rb) / N_SHIFTS * 1e3,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "assess_kernel<float,false> (rebuild)",
+                     "flop_per_launch": flop, "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+        "gpu_launches": launches, "fp64_solves": n64, "degenerate": ndeg, "clocks": clk,
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if rank == 0 and world_size == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(world_np, origins, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line))
+    if world_size > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_e2e(seb, m, world_np, origins, args, dev):
+    """Same step through the C ABI with host buffers: every window is copied host -> device
+    from pinned memory before its update/shift, and the map's outputs (5 channels + flags)
+    are read back to pinned host memory at the end of the step."""
+    import torch
+
+    host_wins = [torch.from_numpy(np.ascontiguousarray(world_np[o[1]:o[1] + NY, o[0]:o[0] + NX])).pin_memory()
+                 for o in origins]
+    dwin = torch.empty((NY, NX), dtype=torch.float32, device=dev)
+    dwin2 = torch.empty_like(dwin)
+    hout = torch.empty(m.out_phys.numel(), dtype=torch.float32).pin_memory()
+    hfl = torch.empty(m.flags_phys.numel(), dtype=torch.uint8).pin_memory()
+    stream = torch.cuda.current_stream(dev)
+    h2d = sum(w.numel() * 4 for w in host_wins)
+    d2h = hout.numel() * 4 + hfl.numel()
+
+    def step():
+        cells = 0
+        for i, (hw, o) in enumerate(zip(host_wins, origins)):
+            d = dwin if i % 2 == 0 else dwin2
+            d.copy_(hw, non_blocking=True)
+            if i == 0:
+                m.update(d, o)
+            else:
+                m.shift(d, o)
+            cells += m.view().last_cells
+        hout.copy_(m.out_phys.reshape(-1), non_blocking=True)
+        hfl.copy_(m.flags_phys.reshape(-1), non_blocking=True)
+        return cells
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    total = 0.0
+    cells = 0
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cells += step()
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    ws = int(os.environ.get("WORLD_SIZE", 1))
+    return {"value": cells * ws / (total / 1e3), "unit": "SE(2) cells/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": total / args.steps}
+
+
+if __name__ == "__main__":
+    main()

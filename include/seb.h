@@ -92,7 +92,8 @@ typedef struct {
   int32_t n_min;      /* minimum known footprint cells; 0 = max(3, ceil(N_k / 2)) per bin */
   int32_t elev_dtype; /* SEB_F32 | SEB_BF16 | SEB_F16 */
   int32_t precision;  /* SEB_PLAIN_F32 | SEB_COMPENSATED */
-  float gap_fp64;     /* relative eigen-gap below which the eigen-solve is redone in FP64 */
+  float gap_fp64;     /* relative eigen-gap (lambda_mid - lambda_min) / trace below which the
+                         covariance and eigen-solve are redone in FP64 (default 1e-2) */
 } seb_params;
 
 /* Device pointers into a map's workspace, valid until the next update/shift/destroy. */
@@ -105,6 +106,7 @@ typedef struct {
   int64_t origin_j;
   size_t out_offset;  /* byte offsets of out / flags from the workspace base */
   size_t flags_offset;
+  int64_t last_cells; /* SE(2) cells (c, r, k) the last update/shift recomputed */
 } seb_view;
 
 /* Fills p with the defaults above (c1 geometry: 100 x 100 at 0.1 m, 36 bins, 0.6 x 0.4 m). */
@@ -191,7 +193,7 @@ int seb_query_poses(const seb_params* p, const void* elev_dev, int64_t origin_i,
 
 /*
  * Hand-written adjoint of seb_query_poses: grad_pose[i] = sum_ch grad_out[i][ch] *
- * d out[i][ch] / d pose[i] for ch in (z, pitch, roll, risk) (grad_out [n][4]).  The set of
+ * d out[i][ch] / d pose[i] over the five output channels (grad_out [n][SEB_N_CH]).  The set of
  * known lattice points is held fixed; the risk gradient is 0 on the clamped (risk = 1)
  * branches and sign(0) = 0 at |.| kinks.  saved_dev may be NULL (recomputed).
  */

@@ -108,7 +108,7 @@ def _load():
             i64 = ctypes.c_int64
             lib.orc_footprint.argtypes = [P, ctypes.c_int, ip, ip, ctypes.c_int]
             lib.orc_jacobi3.argtypes = [dp, dp, dp]
-            lib.orc_grid.argtypes = [P, dp, i64, i64, dp, u8p, ctypes.c_int]
+            lib.orc_grid.argtypes = [P, dp, i64, i64, dp, u8p, dp, ctypes.c_int]
             lib.orc_cells.argtypes = [P, dp, i64, i64, i32p, i64, dp, u8p, dp, ctypes.c_int]
             lib.orc_cell_detail.argtypes = [P, dp, i64, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
             lib.orc_poses.argtypes = [P, dp, i64, i64, dp, i64, dp, u8p, ctypes.c_int]
@@ -158,18 +158,21 @@ def jacobi3(A: np.ndarray):
     return ev, V.reshape(3, 3)
 
 
-def assess_grid(params: OracleParams, elev, origin=(0, 0), n_threads=None):
-    """Every (c, r, k): returns out [5][n_yaw][ny][nx] (z, pitch, roll, rough, risk), flags."""
+def assess_grid(params: OracleParams, elev, origin=(0, 0), n_threads=None, with_gap=False):
+    """Every (c, r, k): returns out [5][n_yaw][ny][nx] (z, pitch, roll, rough, risk), flags
+    [n_yaw][ny][nx], and with_gap=True also the relative eigen-gap [n_yaw][ny][nx]."""
     lib = _load()
     e = _elev(params, elev)
     out = np.zeros((5, params.n_yaw, params.ny, params.nx))
     flags = np.zeros((params.n_yaw, params.ny, params.nx), np.uint8)
+    gap = np.zeros((params.n_yaw, params.ny, params.nx)) if with_gap else None
     p = params._c()
     rc = lib.orc_grid(ctypes.byref(p), _ptr(e, ctypes.c_double), origin[0], origin[1],
-                      _ptr(out, ctypes.c_double), _ptr(flags, ctypes.c_uint8), _threads(n_threads))
+                      _ptr(out, ctypes.c_double), _ptr(flags, ctypes.c_uint8),
+                      _ptr(gap, ctypes.c_double) if with_gap else None, _threads(n_threads))
     if rc != 0:
         raise ValueError("oracle: bad parameters")
-    return out, flags
+    return (out, flags, gap) if with_gap else (out, flags)
 
 
 def assess_cells(params: OracleParams, elev, cells, origin=(0, 0), n_threads=None):
@@ -224,11 +227,11 @@ def query_poses(params: OracleParams, elev, poses, origin=(0, 0), n_threads=None
 
 
 def query_poses_vjp(params: OracleParams, elev, poses, grad_out, origin=(0, 0), n_threads=None):
-    """Gradient of sum(grad_out * (z, pitch, roll, risk)) w.r.t. poses: [n][3]."""
+    """Gradient of sum(grad_out * (z, pitch, roll, rough, risk)) w.r.t. poses: [n][3]."""
     lib = _load()
     e = _elev(params, elev)
     poses = np.ascontiguousarray(poses, np.float64).reshape(-1, 3)
-    g = np.ascontiguousarray(grad_out, np.float64).reshape(-1, 4)
+    g = np.ascontiguousarray(grad_out, np.float64).reshape(-1, 5)
     n = poses.shape[0]
     gp = np.zeros((n, 3))
     p = params._c()

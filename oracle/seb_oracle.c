@@ -342,6 +342,7 @@ typedef struct {
   /* grid mode */
   double* out;
   uint8_t* flags;
+  double* gapg;
   int row0, row1;
   /* list mode */
   const int32_t* cells;
@@ -360,10 +361,12 @@ static void* grid_worker(void* arg) {
     for (int k = 0; k < P->n_yaw; ++k)
       for (int c = 0; c < P->nx; ++c) {
         double o[5];
-        int f = assess_cell(P, J->T, J->elev, J->oi, J->oj, c, r, k, pts, o, NULL);
+        orc_detail D;
+        int f = assess_cell(P, J->T, J->elev, J->oi, J->oj, c, r, k, pts, o, &D);
         int64_t idx = (int64_t)k * plane + (int64_t)r * P->nx + c;
         for (int ch = 0; ch < 5; ++ch) J->out[ch * chs + idx] = o[ch];
         J->flags[idx] = (uint8_t)f;
+        if (J->gapg) J->gapg[idx] = D.n >= 3 ? D.gap : NAN;
       }
   free(pts);
   return NULL;
@@ -376,9 +379,10 @@ static int max_table(const orc_params* P, const orc_table* T) {
 }
 
 /* Full window: out is [5][n_yaw][ny][nx] (z, pitch, roll, roughness, risk), flags
- * [n_yaw][ny][nx].  Returns 0, or -1 on bad parameters. */
+ * [n_yaw][ny][nx], gap [n_yaw][ny][nx] (may be NULL) the relative eigen-gap
+ * (lambda_mid - lambda_min) / trace.  Returns 0, or -1 on bad parameters. */
 int orc_grid(const orc_params* P, const double* elev, int64_t oi, int64_t oj, double* out,
-             uint8_t* flags, int n_threads) {
+             uint8_t* flags, double* gap, int n_threads) {
   if (P->n_yaw < 2 || (P->n_yaw & 1) || P->nx <= 0 || P->ny <= 0) return -1;
   orc_table* T = (orc_table*)calloc(P->n_yaw, sizeof(orc_table));
   if (build_tables(P, T)) return -1;
@@ -395,6 +399,7 @@ int orc_grid(const orc_params* P, const double* elev, int64_t oi, int64_t oj, do
     J->oj = oj;
     J->out = out;
     J->flags = flags;
+    J->gapg = gap;
     J->row0 = (int)((int64_t)P->ny * t / n_threads);
     J->row1 = (int)((int64_t)P->ny * (t + 1) / n_threads);
     J->max_n = max_table(P, T);
@@ -592,7 +597,7 @@ static void* pose_worker(void* arg) {
   int* lat = (int*)malloc(sizeof(int) * 2 * m);
   for (int64_t i = J->i0; i < J->i1; ++i) {
     if (J->gpose) {
-      pose_vjp_one(J->P, J->L, J->elev, J->oi, J->oj, J->poses + 3 * i, J->gout + 4 * i,
+      pose_vjp_one(J->P, J->L, J->elev, J->oi, J->oj, J->poses + 3 * i, J->gout + 5 * i,
                    J->gpose + 3 * i, pts, dz, lat);
     } else {
       double o[5];
@@ -650,8 +655,8 @@ int orc_poses(const orc_params* P, const double* elev, int64_t oi, int64_t oj,
 }
 
 /*
- * Reverse-mode gradient of (z, pitch, roll, risk) with respect to the pose (x, y, yaw),
- * contracted with gout [n][4].  The valid point set is held fixed (points whose bilinear
+ * Reverse-mode gradient of (z, pitch, roll, roughness, risk) with respect to the pose
+ * (x, y, yaw), contracted with gout [n][5].  The valid point set is held fixed (points whose bilinear
  * corners are all known); derivatives are one-sided at |.| kinks (sign(0) = 0) and zero
  * on the clamped risk = 1 branches.  Written directly from the forward definitions:
  *   C = (1/N) sum (P_i - m)(P_i - m)^T, z_b = +-v_min, d lambda_min = n^T dC n,
@@ -676,13 +681,13 @@ static void pose_vjp_one(const orc_params* P, const orc_lattice* L, const double
   double lam0 = D.evals[0];
   double pitch = out[1], roll = out[2];
 
-  double kb = 0.0, pb = g[1], rb = g[2];
+  double kb = g[3], pb = g[1], rb = g[2];
   if (!(flags & ORC_OBSTACLE)) {
     double sp = pitch > 0 ? 1.0 : (pitch < 0 ? -1.0 : 0.0);
     double sr = roll > 0 ? 1.0 : (roll < 0 ? -1.0 : 0.0);
-    kb += g[3] * P->w[0] / P->kappa_max;
-    pb += g[3] * P->w[1] * sp / P->phi_x_max;
-    rb += g[3] * P->w[2] * sr / P->phi_y_max;
+    kb += g[4] * P->w[0] / P->kappa_max;
+    pb += g[4] * P->w[1] * sp / P->phi_x_max;
+    rb += g[4] * P->w[2] * sr / P->phi_y_max;
   }
   double xbb[3] = {0, 0, pb / sqrt(1.0 - xb[2] * xb[2])};
   double ybb[3] = {0, 0, rb / sqrt(1.0 - yb[2] * yb[2])};
@@ -749,7 +754,7 @@ static void pose_vjp_one(const orc_params* P, const orc_lattice* L, const double
   gp[2] = gth;
 }
 
-/* Gradient for n poses: gout [n][4] (z, pitch, roll, risk) -> gpose [n][3]. */
+/* Gradient for n poses: gout [n][5] (z, pitch, roll, roughness, risk) -> gpose [n][3]. */
 int orc_poses_vjp(const orc_params* P, const double* elev, int64_t oi, int64_t oj,
                   const double* poses, int64_t n, const double* gout, double* gpose,
                   int n_threads) {

@@ -83,6 +83,7 @@ class seb_view(ctypes.Structure):
         ("origin_j", ctypes.c_int64),
         ("out_offset", ctypes.c_size_t),
         ("flags_offset", ctypes.c_size_t),
+        ("last_cells", ctypes.c_int64),
     ]
 
 
@@ -220,3 +221,4 @@ def seb_query_poses_backward(p: seb_params, elev_ptr, origin_i, origin_j, poses_
                              grad_out_ptr, grad_pose_ptr, n, stream=0) -> None:
     _check(load().seb_query_poses_backward(ctypes.byref(p), elev_ptr, origin_i, origin_j, poses_ptr,
                                            saved_ptr, grad_out_ptr, grad_pose_ptr, n, stream))
+

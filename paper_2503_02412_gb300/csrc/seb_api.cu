@@ -25,6 +25,7 @@ struct seb_map {
   seb::Control* ctl;
   int32_t ring_x, ring_y;
   int64_t oi, oj;
+  int64_t last_cells;
   bool valid;
   char err[256];
 };
@@ -74,22 +75,41 @@ static Launch base_launch(const seb_map* m, const void* elev) {
   L.w1 = m->p.w[1];
   L.w2 = m->p.w[2];
   L.gap_fp64 = m->p.gap_fp64;
-  int sw = kTileW + 2 * m->T.rx;
-  if ((sw & 1) == 0) ++sw;  // odd row pitch: the 4 rows a warp touches hit distinct banks
-  L.sw = sw;
-  L.sh = kTileH + 2 * m->T.ry;
+  L.narrow_moments = m->T.narrow;
   L.err = &m->ctl->err;
   L.counters = &m->ctl->n_fp64;
   return L;
 }
 
-static void add_rect(Launch& L, int x0, int y0, int w, int h) {
+static void push_rect(Launch& L, int x0, int y0, int w, int h, int lg) {
   if (w <= 0 || h <= 0) return;
   const int i = L.n_rects++;
-  L.rects[i] = Rect{x0, y0, w, h};
-  L.tiles_x[i] = (w + kTileW - 1) / kTileW;
-  const int ty = (h + kTileH - 1) / kTileH;
-  L.tile_start[i + 1] = L.tile_start[i] + L.tiles_x[i] * ty;
+  L.rects[i] = Rect{x0, y0, w, h, lg};
+  const int tw = kG << lg, th = kThreads >> lg;
+  L.tiles_x[i] = (w + tw - 1) / tw;
+  L.tile_start[i + 1] = L.tile_start[i] + L.tiles_x[i] * ((h + th - 1) / th);
+}
+
+// A rectangle of cells to recompute, split so that no tile is mostly empty: whole 32 x 32
+// tiles, a right remainder in 8-wide tiles and a bottom remainder in 8-tall tiles.
+static void add_rect(Launch& L, int x0, int y0, int w, int h) {
+  if (w <= 0 || h <= 0) return;
+  const int wm = w >= 32 ? w - w % 32 : 0, hm = h >= 32 ? h - h % 32 : 0;
+  if (wm && hm) {
+    push_rect(L, x0, y0, wm, hm, 3);
+    push_rect(L, x0 + wm, y0, w - wm, h, 1);
+    push_rect(L, x0, y0 + hm, wm, h - hm, 5);
+  } else if (w < h) {
+    push_rect(L, x0, y0, w, h, 1);
+  } else {
+    push_rect(L, x0, y0, w, h, 5);
+  }
+}
+
+static int64_t rect_cells(const Launch& L, int n_yaw) {
+  int64_t c = 0;
+  for (int i = 0; i < L.n_rects; ++i) c += (int64_t)L.rects[i].w * L.rects[i].h;
+  return c * n_yaw;
 }
 
 static int check_elev(seb_map* m, const void* elev) {
@@ -128,7 +148,7 @@ void seb_params_default(seb_params* p) {
   p->n_min = 0;
   p->elev_dtype = SEB_F32;
   p->precision = SEB_PLAIN_F32;
-  p->gap_fp64 = 1e-6f;
+  p->gap_fp64 = 1e-2f;
 }
 
 const char* seb_status_string(int s) {
@@ -203,6 +223,7 @@ int seb_map_update(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
   add_rect(L, 0, 0, m->p.nx, m->p.ny);
   cudaError_t e = launch_assess(m->T, L, m->p.elev_dtype, m->p.precision, m->stream);
   if (e != cudaSuccess) return cuda_fail(m, e, "assess launch");
+  m->last_cells = rect_cells(L, m->p.n_yaw);
   m->oi = oi;
   m->oj = oj;
   m->valid = true;
@@ -217,7 +238,10 @@ int seb_map_shift(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
   const int64_t dx = oi - m->oi, dy = oj - m->oj;
   const int nx = m->p.nx, ny = m->p.ny;
   if (dx >= nx || -dx >= nx || dy >= ny || -dy >= ny) return seb_map_update(m, elev, oi, oj);
-  if (dx == 0 && dy == 0) return SEB_OK;
+  if (dx == 0 && dy == 0) {
+    m->last_cells = 0;
+    return SEB_OK;
+  }
   // Logical cell c of the new window is logical c + dx of the old one; the ring offset
   // keeps every surviving cell at its physical address.
   m->ring_x = (int32_t)(((m->ring_x + dx) % nx + nx) % nx);
@@ -251,6 +275,7 @@ int seb_map_shift(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
   }
   cudaError_t e = launch_assess(m->T, L, m->p.elev_dtype, m->p.precision, m->stream);
   if (e != cudaSuccess) return cuda_fail(m, e, "assess launch (shift)");
+  m->last_cells = rect_cells(L, m->p.n_yaw);
   m->oi = oi;
   m->oj = oj;
   return SEB_OK;
@@ -266,6 +291,7 @@ int seb_map_view(const seb_map* m, seb_view* v) {
   v->origin_j = m->oj;
   v->out_offset = (size_t)((uint8_t*)m->out - m->ws);
   v->flags_offset = (size_t)(m->flags - m->ws);
+  v->last_cells = m->last_cells;
   return SEB_OK;
 }
 

@@ -46,15 +46,23 @@ __device__ __noinline__ Cell finish_cell(int N, int MX, int MY, int MXX, int MXY
   const float res = L.res;
   const float fN = (float)N;
   const float inv_n2 = 1.f / (fN * fN);
-  // N^2 Cov_xy-block numerators are exact integers.
-  const long long nxx = (long long)N * MXX - (long long)MX * MX;
-  const long long nxy = (long long)N * MXY - (long long)MX * MY;
-  const long long nyy = (long long)N * MYY - (long long)MY * MY;
+  // N^2 Cov_xy-block numerators are exact integers (int32 when the tables allow it: 64-bit
+  // integer conversions run on the FP64 unit).
+  float nxx, nxy, nyy;
+  if (L.narrow_moments) {
+    nxx = (float)(N * MXX - MX * MX);
+    nxy = (float)(N * MXY - MX * MY);
+    nyy = (float)(N * MYY - MY * MY);
+  } else {
+    nxx = (float)((long long)N * MXX - (long long)MX * MX);
+    nxy = (float)((long long)N * MXY - (long long)MX * MY);
+    nyy = (float)((long long)N * MYY - (long long)MY * MY);
+  }
   const float fMX = (float)MX, fMY = (float)MY;
   float c[6];
-  c[0] = (float)nxx * inv_n2 * res * res;
-  c[1] = (float)nxy * inv_n2 * res * res;
-  c[3] = (float)nyy * inv_n2 * res * res;
+  c[0] = nxx * inv_n2 * res * res;
+  c[1] = nxy * inv_n2 * res * res;
+  c[3] = nyy * inv_n2 * res * res;
   c[2] = fmaf(S1, fN, -fMX * S0) * inv_n2 * res;
   c[4] = fmaf(S2, fN, -fMY * S0) * inv_n2 * res;
   c[5] = fmaf(S3, fN, -S0 * S0) * inv_n2;
@@ -62,35 +70,28 @@ __device__ __noinline__ Cell finish_cell(int N, int MX, int MY, int MXX, int MXY
   min_eigpair<float>(c, n, &gap);
   uint32_t flags = 0;
   const float tr = c[0] + c[3] + c[5];
-  float lam;
   if (gap < L.gap_fp64) {
-    // Near-degenerate: covariance and eigen-solve again in FP64 from the same moments.
+    // Small relative eigen-gap: covariance and eigen-solve again in FP64 from the same moments.
     flags |= SEB_FLAG_FP64;
     const double dN = (double)N, i2 = 1.0 / (dN * dN), r = (double)res;
     double cd[6];
-    cd[0] = (double)nxx * i2 * r * r;
-    cd[1] = (double)nxy * i2 * r * r;
-    cd[3] = (double)nyy * i2 * r * r;
+    cd[0] = ((double)N * MXX - (double)MX * MX) * i2 * r * r;
+    cd[1] = ((double)N * MXY - (double)MX * MY) * i2 * r * r;
+    cd[3] = ((double)N * MYY - (double)MY * MY) * i2 * r * r;
     cd[2] = ((double)S1 * dN - (double)MX * (double)S0) * i2 * r;
     cd[4] = ((double)S2 * dN - (double)MY * (double)S0) * i2 * r;
     cd[5] = ((double)S3 * dN - (double)S0 * (double)S0) * i2;
     double nd[3], gd;
     min_eigpair<double>(cd, nd, &gd);
-    const double ld = cd[0] * nd[0] * nd[0] + cd[3] * nd[1] * nd[1] + cd[5] * nd[2] * nd[2] +
-                      2.0 * (cd[1] * nd[0] * nd[1] + cd[2] * nd[0] * nd[2] + cd[4] * nd[1] * nd[2]);
-    const double trd = cd[0] + cd[3] + cd[5];
+    const double ld = refine_min<double>(cd, nd);
     n[0] = (float)nd[0];
     n[1] = (float)nd[1];
     n[2] = (float)nd[2];
-    lam = (float)(ld > 0.0 ? ld : 0.0);
-    o.rough = (float)((ld > 0.0 ? ld : 0.0) / trd);
+    o.rough = (float)(ld / (cd[0] + cd[3] + cd[5]));
     atomicAdd(&L.counters[0], 1ull);
     if (gd < 1e-12) flags |= SEB_FLAG_DEGENERATE;
   } else {
-    lam = c[0] * n[0] * n[0] + c[3] * n[1] * n[1] + c[5] * n[2] * n[2] +
-          2.f * (c[1] * n[0] * n[1] + c[2] * n[0] * n[2] + c[4] * n[1] * n[2]);
-    lam = fmaxf(lam, 0.f);
-    o.rough = lam / tr;
+    o.rough = refine_min<float>(c, n) / tr;
   }
   // Body frame (Eqs. 2-3): u = z_b x x_yaw = (-n_z s, n_z c, n_x s - n_y c),
   // y_b = u / |u|, x_b = y_b x z_b, so b3^T x_b = -n_z (n_x c + n_y s) / |u|.
@@ -119,70 +120,128 @@ __device__ __noinline__ Cell finish_cell(int N, int MX, int MY, int MXX, int MXY
     o.risk = L.w0 * (o.rough / L.kappa_max) + L.w1 * (ap / L.phi_x_max) + L.w2 * (ar / L.phi_y_max);
   }
   o.flags = flags;
-  (void)lam;
   return o;
 }
 
 __device__ __forceinline__ int unpack(uint32_t v, int sh) { return (int)((v >> sh) & 0xffu) - 128; }
 
-// Moments of the 4 cells of this thread for yaw pair `pair`.
-template <bool MASKED, bool COMP>
-__device__ __forceinline__ void accumulate(const Tables& T, int pair, const float* __restrict__ sc,
-                                           int sw, const float ref[kG], float S0[kG], float S1[kG],
-                                           float S2[kG], float S3[kG], int N[kG], int MX[kG],
-                                           int MY[kG], int MXX[kG], int MXY[kG], int MYY[kG]) {
-  float C0[kG], C1[kG], C2[kG], C3[kG];  // compensation terms
-  float fN[kG], fMX[kG], fMY[kG], fMXX[kG], fMXY[kG], fMYY[kG];
+// Moments of the kG cells of this thread for yaw pair `pair`, run by run.  A run whose rows
+// (over the warp's cells) hold no unknown cell takes the plain path: 4 FP32 operations per
+// (point, cell).  Otherwise the masked path replaces unknown heights by 0 with a 0 weight
+// (z' = fma(-ref, m, z_known), exactly z - ref for known points) and accumulates the integer
+// moments of the missing points, Q = (n, sum di, sum dj, sum di^2, sum di dj, sum dj^2), which
+// are later subtracted from the table's.  Both paths give bit-identical moments for a run
+// without unknown cells, so the choice (made per warp) never changes a result.
+template <bool COMP>
+__device__ __forceinline__ void accumulate(const Tables& T, int pair, const float* __restrict__ sc, int sw,
+                                           const int* __restrict__ rowflag_warp, int rpw,
+                                           const float ref[kG], float S0[kG], float S1[kG], float S2[kG],
+                                           float S3[kG], float Q[6][kG]) {
+  float C0[kG], C1[kG], C2[kG], C3[kG];  // compensation terms (COMP)
 #pragma unroll
   for (int g = 0; g < kG; ++g) {
     S0[g] = S1[g] = S2[g] = S3[g] = 0.f;
     C0[g] = C1[g] = C2[g] = C3[g] = 0.f;
-    fN[g] = fMX[g] = fMY[g] = fMXX[g] = fMXY[g] = fMYY[g] = 0.f;
+#pragma unroll
+    for (int t = 0; t < 6; ++t) Q[t][g] = 0.f;
   }
+  const int lane = threadIdx.x & 31;
   const int r0 = T.run_start[pair], r1 = T.run_start[pair + 1];
   for (int q = r0; q < r1; ++q) {
     const uint32_t pk = T.runs[q];
     const int dj = unpack(pk, 0), lo = unpack(pk, 8), hi = unpack(pk, 16);
+    int f = 0;
+    for (int r = lane; r < rpw; r += 32) f |= rowflag_warp[dj + r];
+    const bool masked = __any_sync(0xffffffffu, f);
     const float* p = sc + dj * sw + lo;
-    float a[kG], ac[kG], b[kG], bc[kG], s3[kG], s3c[kG], cn[kG], cx[kG];
-#pragma unroll
-    for (int g = 0; g < kG; ++g) a[g] = ac[g] = b[g] = bc[g] = s3[g] = s3c[g] = cn[g] = cx[g] = 0.f;
-    float w0 = p[0], w1 = p[1], w2 = p[2];
-    float di = (float)lo;
     const int len = hi - lo + 1;
+    float a[kG], ac[kG], b[kG], bc[kG], s3[kG], s3c[kG];
+#pragma unroll
+    for (int g = 0; g < kG; ++g) a[g] = ac[g] = b[g] = bc[g] = s3[g] = s3c[g] = 0.f;
+    if (!masked) {
+      float w0 = p[0], w1 = p[1], w2 = p[2];
+      float di = (float)lo;
 #pragma unroll 2
-    for (int i = 0; i < len; ++i) {
-      const float w3 = p[i + 3];
-      const float wv[kG] = {w0, w1, w2, w3};
+      for (int i = 0; i < len; ++i) {
+        const float w3 = p[i + 3];
+        const float wv[kG] = {w0, w1, w2, w3};
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+          const float zp = wv[g] - ref[g];
+          if (COMP) {
+            nadd(a[g], ac[g], zp);
+            nadd(b[g], bc[g], __fmul_rn(di, zp));
+            nadd(s3[g], s3c[g], __fmul_rn(zp, zp));
+          } else {
+            a[g] += zp;
+            b[g] = fmaf(di, zp, b[g]);
+            s3[g] = fmaf(zp, zp, s3[g]);
+          }
+        }
+        w0 = w1;
+        w1 = w2;
+        w2 = w3;
+        di += 1.f;
+      }
+    } else {
+      // window of (known height or 0, known weight, missing weight)
+      float z0, z1, z2, m0, m1, m2, x0, x1, x2;
+      auto split = [](float v, float& z, float& m, float& x) {
+        const bool k = v == v;
+        z = k ? v : 0.f;
+        m = k ? 1.f : 0.f;
+        x = k ? 0.f : 1.f;
+      };
+      split(p[0], z0, m0, x0);
+      split(p[1], z1, m1, x1);
+      split(p[2], z2, m2, x2);
+      float qn[kG], qx[kG], qxx[kG];
+#pragma unroll
+      for (int g = 0; g < kG; ++g) qn[g] = qx[g] = qxx[g] = 0.f;
+      float di = (float)lo;
+#pragma unroll 2
+      for (int i = 0; i < len; ++i) {
+        float z3, m3, x3;
+        split(p[i + 3], z3, m3, x3);
+        const float zs[kG] = {z0, z1, z2, z3}, ms[kG] = {m0, m1, m2, m3}, xs[kG] = {x0, x1, x2, x3};
+        const float di2 = di * di;
+#pragma unroll
+        for (int g = 0; g < kG; ++g) {
+          const float zp = fmaf(-ref[g], ms[g], zs[g]);
+          if (COMP) {
+            nadd(a[g], ac[g], zp);
+            nadd(b[g], bc[g], __fmul_rn(di, zp));
+            nadd(s3[g], s3c[g], __fmul_rn(zp, zp));
+          } else {
+            a[g] += zp;
+            b[g] = fmaf(di, zp, b[g]);
+            s3[g] = fmaf(zp, zp, s3[g]);
+          }
+          qn[g] += xs[g];
+          qx[g] = fmaf(di, xs[g], qx[g]);
+          qxx[g] = fmaf(di2, xs[g], qxx[g]);
+        }
+        z0 = z1;
+        z1 = z2;
+        z2 = z3;
+        m0 = m1;
+        m1 = m2;
+        m2 = m3;
+        x0 = x1;
+        x1 = x2;
+        x2 = x3;
+        di += 1.f;
+      }
+      const float fdj = (float)dj;
 #pragma unroll
       for (int g = 0; g < kG; ++g) {
-        float zp, m = 1.f;
-        if (MASKED) {
-          const bool known = wv[g] == wv[g];
-          m = known ? 1.f : 0.f;
-          zp = fmaf(-ref[g], m, known ? wv[g] : 0.f);
-        } else {
-          zp = wv[g] - ref[g];
-        }
-        if (COMP) {
-          nadd(a[g], ac[g], zp);
-          nadd(b[g], bc[g], __fmul_rn(di, zp));
-          nadd(s3[g], s3c[g], __fmul_rn(zp, zp));
-        } else {
-          a[g] += zp;
-          b[g] = fmaf(di, zp, b[g]);
-          s3[g] = fmaf(zp, zp, s3[g]);
-        }
-        if (MASKED) {
-          cn[g] += m;
-          cx[g] = fmaf(di, m, cx[g]);
-          fMXX[g] = fmaf(di * di, m, fMXX[g]);
-        }
+        Q[0][g] += qn[g];
+        Q[1][g] += qx[g];
+        Q[2][g] = fmaf(fdj, qn[g], Q[2][g]);
+        Q[3][g] += qxx[g];
+        Q[4][g] = fmaf(fdj, qx[g], Q[4][g]);
+        Q[5][g] = fmaf(fdj * fdj, qn[g], Q[5][g]);
       }
-      w0 = w1;
-      w1 = w2;
-      w2 = w3;
-      di += 1.f;
     }
     const float fdj = (float)dj;
 #pragma unroll
@@ -199,37 +258,15 @@ __device__ __forceinline__ void accumulate(const Tables& T, int pair, const floa
         S2[g] = fmaf(fdj, a[g], S2[g]);
         S3[g] += s3[g];
       }
-      if (MASKED) {
-        fN[g] += cn[g];
-        fMX[g] += cx[g];
-        fMY[g] = fmaf(fdj, cn[g], fMY[g]);
-        fMYY[g] = fmaf(fdj * fdj, cn[g], fMYY[g]);
-        fMXY[g] = fmaf(fdj, cx[g], fMXY[g]);
-      }
     }
   }
+  if (COMP) {
 #pragma unroll
-  for (int g = 0; g < kG; ++g) {
-    if (COMP) {
+    for (int g = 0; g < kG; ++g) {
       S0[g] += C0[g];
       S1[g] += C1[g];
       S2[g] += C2[g];
       S3[g] += C3[g];
-    }
-    if (MASKED) {
-      N[g] = (int)fN[g];
-      MX[g] = (int)fMX[g];
-      MY[g] = (int)fMY[g];
-      MXX[g] = (int)fMXX[g];
-      MXY[g] = (int)fMXY[g];
-      MYY[g] = (int)fMYY[g];
-    } else {
-      N[g] = T.mom[pair][0];
-      MX[g] = T.mom[pair][1];
-      MY[g] = T.mom[pair][2];
-      MXX[g] = T.mom[pair][3];
-      MXY[g] = T.mom[pair][4];
-      MYY[g] = T.mom[pair][5];
     }
   }
 }
@@ -237,39 +274,46 @@ __device__ __forceinline__ void accumulate(const Tables& T, int pair, const floa
 template <typename E, bool COMP>
 __global__ void __launch_bounds__(kThreads, 2)
     assess_kernel(const __grid_constant__ Tables T, const __grid_constant__ Launch L) {
-  extern __shared__ float tile[];
+  extern __shared__ float smem[];
+  int* rowflag = reinterpret_cast<int*>(smem);  // per staged row: holds an unknown cell
+  float* tile = smem + kMaxStageRows;
   if (blockDim.x != kThreads || blockIdx.y >= (unsigned)T.n_pairs) {
     if (threadIdx.x == 0) atomicOr(L.err, kErrLaunchShape);
     return;
   }
-  // Which rectangle and tile this CTA covers.
+  // Which rectangle and tile this CTA covers, and the rectangle's layout.
   const int b = blockIdx.x;
   int ri = 0;
 #pragma unroll 1
   while (ri + 1 < L.n_rects && b >= L.tile_start[ri + 1]) ++ri;
   const Rect R = L.rects[ri];
+  const int lg = R.log_tpr;
+  const int tw = kG << lg, th = kThreads >> lg;
   const int t = b - L.tile_start[ri];
-  const int tx0 = R.x0 + (t % L.tiles_x[ri]) * kTileW;
-  const int ty0 = R.y0 + (t / L.tiles_x[ri]) * kTileH;
-  const int rx = T.rx, ry = T.ry, sw = L.sw, sh = L.sh;
+  const int tx0 = R.x0 + (t % L.tiles_x[ri]) * tw;
+  const int ty0 = R.y0 + (t / L.tiles_x[ri]) * th;
+  const int rx = T.rx, ry = T.ry;
+  const int sw = stage_w(lg, rx), sh = stage_h(lg, ry);
 
+  for (int i = threadIdx.x; i < sh; i += kThreads) rowflag[i] = 0;
+  __syncthreads();
   // Stage tile + halo (outside the window = NaN = unknown).
   const E* __restrict__ elev = static_cast<const E*>(L.elev);
   const float qnan = __int_as_float(0x7fc00000);
-  int any_nan = 0;
   for (int idx = threadIdx.x; idx < sw * sh; idx += kThreads) {
     const int row = idx / sw, col = idx - row * sw;
     const int gy = ty0 - ry + row, gx = tx0 - rx + col;
     float v = qnan;
-    if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny)
-      v = to_f32<E>(elev[(int64_t)gy * L.nx + gx]);
-    any_nan |= (v != v);
+    if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) v = to_f32<E>(elev[(int64_t)gy * L.nx + gx]);
+    if (v != v) rowflag[row] = 1;
     tile[idx] = v;
   }
-  any_nan = __syncthreads_or(any_nan);
+  __syncthreads();
 
-  const int lx = (threadIdx.x & 7) * kG;
-  const int ly = threadIdx.x >> 3;
+  const int lx = (threadIdx.x & ((1 << lg) - 1)) * kG;
+  const int ly = threadIdx.x >> lg;
+  const int rpw = 32 >> lg > 0 ? 32 >> lg : 1;  // cell rows per warp
+  const int ly_w0 = (threadIdx.x & ~31) >> lg;
   const int cx = tx0 + lx, cy = ty0 + ly;
   const int pair = blockIdx.y;
   const float* sc = tile + (ry + ly) * sw + rx + lx;  // centre of cell g is sc[g]
@@ -277,35 +321,29 @@ __global__ void __launch_bounds__(kThreads, 2)
   float ref[kG];
 #pragma unroll
   for (int g = 0; g < kG; ++g) ref[g] = sc[g];
-  if (any_nan) {
-    // Unknown centre: the first known cell of the footprint in run order.
 #pragma unroll
-    for (int g = 0; g < kG; ++g) {
-      if (ref[g] == ref[g]) continue;
-      float r = 0.f;
-      bool found = false;
-      for (int q = T.run_start[pair]; q < T.run_start[pair + 1] && !found; ++q) {
-        const uint32_t pk = T.runs[q];
-        const int dj = unpack(pk, 0), lo = unpack(pk, 8), hi = unpack(pk, 16);
-        for (int d = lo; d <= hi; ++d) {
-          const float v = sc[dj * sw + g + d];
-          if (v == v) {
-            r = v;
-            found = true;
-            break;
-          }
+  for (int g = 0; g < kG; ++g) {
+    if (ref[g] == ref[g]) continue;
+    // Unknown centre: the first known cell of the footprint in run order.
+    float r = 0.f;
+    bool found = false;
+    for (int q = T.run_start[pair]; q < T.run_start[pair + 1] && !found; ++q) {
+      const uint32_t pk = T.runs[q];
+      const int dj = unpack(pk, 0), lo = unpack(pk, 8), hi = unpack(pk, 16);
+      for (int d = lo; d <= hi; ++d) {
+        const float v = sc[dj * sw + g + d];
+        if (v == v) {
+          r = v;
+          found = true;
+          break;
         }
       }
-      ref[g] = r;
     }
+    ref[g] = r;
   }
 
-  float S0[kG], S1[kG], S2[kG], S3[kG];
-  int N[kG], MX[kG], MY[kG], MXX[kG], MXY[kG], MYY[kG];
-  if (any_nan)
-    accumulate<true, COMP>(T, pair, sc, sw, ref, S0, S1, S2, S3, N, MX, MY, MXX, MXY, MYY);
-  else
-    accumulate<false, COMP>(T, pair, sc, sw, ref, S0, S1, S2, S3, N, MX, MY, MXX, MXY, MYY);
+  float S0[kG], S1[kG], S2[kG], S3[kG], Q[6][kG];
+  accumulate<COMP>(T, pair, sc, sw, rowflag + ry + ly_w0, rpw, ref, S0, S1, S2, S3, Q);
 
   if (cy >= R.y0 + R.h) return;
   const int k0 = pair, k1 = pair + T.n_pairs;
@@ -313,12 +351,14 @@ __global__ void __launch_bounds__(kThreads, 2)
   int pr = cy + L.ring_y;
   if (pr >= L.ny) pr -= L.ny;
   const int64_t chs = (int64_t)L.n_yaw * L.plane;
+  const int* mom = T.mom[pair];
 #pragma unroll
   for (int g = 0; g < kG; ++g) {
     const int c = cx + g;
     if (c >= R.x0 + R.w) break;
-    const Cell o = finish_cell(N[g], MX[g], MY[g], MXX[g], MXY[g], MYY[g], S0[g], S1[g], S2[g], S3[g],
-                               ref[g], T.n_min[pair], ct, st, L);
+    const Cell o = finish_cell(mom[0] - (int)Q[0][g], mom[1] - (int)Q[1][g], mom[2] - (int)Q[2][g],
+                               mom[3] - (int)Q[3][g], mom[4] - (int)Q[4][g], mom[5] - (int)Q[5][g], S0[g], S1[g],
+                               S2[g], S3[g], ref[g], T.n_min[pair], ct, st, L);
     int pc = c + L.ring_x;
     if (pc >= L.nx) pc -= L.nx;
     const int64_t i0 = (int64_t)k0 * L.plane + (int64_t)pr * L.nx + pc;
@@ -358,7 +398,12 @@ __global__ void copy_out_kernel(const Launch L, float* __restrict__ dst, uint8_t
 
 template <typename E, bool COMP>
 cudaError_t launch_typed(const Tables& T, const Launch& L, cudaStream_t stream) {
-  const size_t smem = (size_t)L.sw * L.sh * sizeof(float);
+  size_t smem = 0;
+  for (int i = 0; i < L.n_rects; ++i) {
+    const size_t s = (size_t)stage_w(L.rects[i].log_tpr, T.rx) * stage_h(L.rects[i].log_tpr, T.ry);
+    smem = s > smem ? s : smem;
+  }
+  smem = (smem + kMaxStageRows) * sizeof(float);
   auto kern = assess_kernel<E, COMP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -369,11 +414,6 @@ cudaError_t launch_typed(const Tables& T, const Launch& L, cudaStream_t stream) 
 
 }  // namespace
 
-size_t assess_smem_bytes(const Tables& T) {
-  int sw = kTileW + 2 * T.rx;
-  if ((sw & 1) == 0) ++sw;
-  return (size_t)sw * (kTileH + 2 * T.ry) * sizeof(float);
-}
 
 cudaError_t launch_assess(const Tables& T, const Launch& L, int elev_dtype, int precision,
                           cudaStream_t stream) {

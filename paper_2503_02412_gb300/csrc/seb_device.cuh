@@ -156,4 +156,29 @@ __device__ __forceinline__ bool null_vector(const F c[6], F lambda, F v[3]) {
   return true;
 }
 
+// Rayleigh quotient n^T A n of a unit vector.
+template <typename F>
+__device__ __forceinline__ F rayleigh(const F c[6], const F n[3]) {
+  return c[0] * n[0] * n[0] + c[3] * n[1] * n[1] + c[5] * n[2] * n[2] +
+         F(2) * (c[1] * n[0] * n[1] + c[2] * n[0] * n[2] + c[4] * n[1] * n[2]);
+}
+
+// One Rayleigh-quotient refinement of the smallest eigenpair: the null vector of
+// (A - n^T A n I) replaces n (kept when the rows are degenerate), oriented to n_z >= 0.
+// Returns the refined n^T A n, clamped at 0.  Near a double smallest eigenvalue the
+// closed-form eigenvalue loses accuracy (acos at r ~ -1); the quotient of the first vector
+// is accurate to the square of its angle error, and the refined vector follows it.
+template <typename F>
+__device__ __forceinline__ F refine_min(const F c[6], F n[3]) {
+  F v[3];
+  if (null_vector<F>(c, rayleigh<F>(c, n), v)) {
+    const F sgn = v[2] < F(0) ? F(-1) : F(1);
+    n[0] = v[0] * sgn;
+    n[1] = v[1] * sgn;
+    n[2] = v[2] * sgn;
+  }
+  const F l = rayleigh<F>(c, n);
+  return l > F(0) ? l : F(0);
+}
+
 }  // namespace seb

@@ -8,22 +8,26 @@
 
 namespace seb {
 
-// Tile of output cells per CTA and the thread layout inside it: 256 threads, each owning
-// G = 4 adjacent cells of one row (8 threads per row, 32 rows).
-constexpr int kTileW = 32;
-constexpr int kTileH = 32;
+// Thread layout of a CTA: 256 threads, each owning kG = 4 adjacent cells of one row, with
+// 2^log_tpr threads per row.  log_tpr = 3: 32 x 32 cells (interior); 1: 8 x 128 (narrow
+// column bands); 5: 128 x 8 (narrow row bands).  A warp always spans the full tile width.
 constexpr int kThreads = 256;
 constexpr int kG = 4;
+constexpr int kMaxStageRows = 384;  // staged rows of any layout: 128 + 2 * 127 < 384
+
+__host__ __device__ inline int stage_w(int log_tpr, int rx) { return ((kG << log_tpr) + 2 * rx) | 1; }
+__host__ __device__ inline int stage_h(int log_tpr, int ry) { return (kThreads >> log_tpr) + 2 * ry; }
 
 constexpr int kMaxPairs = 128;  // n_yaw <= 256; bins k and k + n_yaw/2 share a footprint
 constexpr int kMaxRuns = 3072;  // total row runs over all yaw pairs
-constexpr int kMaxRects = 4;    // rolling update: two column bands + two row bands
+constexpr int kMaxRects = 12;   // rolling update: up to 4 bands, each split by layout
 
 // Footprint tables of every yaw pair (Algorithm 1, FindEllipticalPoints, restated as row
 // runs).  Passed to the kernels as a __grid_constant__ parameter, so it lives in the
 // constant bank and its uniform reads are broadcast.
 struct Tables {
   int32_t n_pairs;
+  int32_t narrow;                    // (max N * max reach)^2 < 2^31: int32 covariance numerators
   int32_t rx, ry;                    // largest |di| / |dj| over every footprint
   int32_t run_start[kMaxPairs + 1];  // runs of pair p: [run_start[p], run_start[p+1])
   int32_t n_min[kMaxPairs];          // known cells needed to assess (per bin)
@@ -34,6 +38,7 @@ struct Tables {
 
 struct Rect {
   int32_t x0, y0, w, h;
+  int32_t log_tpr;  // layout: log2 of threads per row
 };
 
 // Everything else a launch needs (by value, in the parameter bank).
@@ -49,11 +54,11 @@ struct Launch {
   float kappa_max, phi_x_max, phi_y_max;
   float w0, w1, w2;
   float gap_fp64;
+  int32_t narrow_moments;  // N * sum di^2 etc. fit in int32
   int32_t n_rects;
   Rect rects[kMaxRects];
   int32_t tile_start[kMaxRects + 1];
   int32_t tiles_x[kMaxRects];
-  int32_t sw, sh;  // staged tile: sw columns (odd, for conflict-free banks) x sh rows
   uint32_t* err;
   unsigned long long* counters;  // [0] FP64 eigen-solves, [1] degenerate cells
 };
@@ -106,7 +111,6 @@ cudaError_t launch_assess(const Tables& T, const Launch& L, int elev_dtype, int 
                           cudaStream_t stream);
 cudaError_t launch_copy_out(const Launch& L, float* out_dev, uint8_t* flags_dev,
                             cudaStream_t stream);
-size_t assess_smem_bytes(const Tables& T);
 
 void set_error(const char* fmt, ...);
 

@@ -14,8 +14,8 @@
 // l, l + GL, ...; the 10 moment sums are reduced with warp shuffles, and every lane of the
 // group then runs the (cheap) eigen-solve, so no shared memory is needed.
 //
-// Backward (reverse mode, valid set held fixed): with g = d loss / d (z, pitch, roll, risk)
-//   - risk: zero on the clamped branches, else w . (kappa/kappa_max, |pitch|/phi_x_max,
+// Backward (reverse mode, valid set held fixed): g = d loss / d (z, pitch, roll, rough, risk)
+//   - roughness = lambda_min / trace directly; risk: zero on the clamped branches, else w . (kappa/kappa_max, |pitch|/phi_x_max,
 //     |roll|/phi_y_max) with sign(0) = 0;
 //   - pitch = asin(x_b,z), roll = asin(y_b,z); x_b = y_b x n; y_b = u/|u|, u = n x x_yaw;
 //   - z through mean z, mean (px, py) and n;
@@ -164,13 +164,14 @@ __device__ __forceinline__ void assess_pose(const QTab& Q, const QLaunch& L, int
     double cd[6], nd[3], gd;
     for (int t = 0; t < 6; ++t) cd[t] = (double)S.C[t];
     min_eigpair<double>(cd, nd, &gd);
+    refine_min<double>(cd, nd);
     for (int t = 0; t < 3; ++t) S.n[t] = (float)nd[t];
     if (gd < 1e-12) S.flags |= SEB_FLAG_DEGENERATE;
+  } else {
+    refine_min<float>(S.C, S.n);
   }
   const float* n = S.n;
-  float lam = S.C[0] * n[0] * n[0] + S.C[3] * n[1] * n[1] + S.C[5] * n[2] * n[2] +
-              2.f * (S.C[1] * n[0] * n[1] + S.C[2] * n[0] * n[2] + S.C[4] * n[1] * n[2]);
-  S.lam = fmaxf(lam, 0.f);
+  S.lam = fmaxf(rayleigh<float>(S.C, n), 0.f);
   S.rough = S.lam / tr;
   const float uz = n[0] * s - n[1] * c;
   const float un = sqrtf(n[2] * n[2] + uz * uz);
@@ -279,15 +280,15 @@ __global__ void __launch_bounds__(256) query_bwd_kernel(const __grid_constant__ 
   }
   float gpx = 0.f, gpy = 0.f, gth = 0.f;
   if (!(S.flags & (SEB_FLAG_UNKNOWN | SEB_FLAG_DEGENERATE))) {
-    const float* g = L.gout + 4 * ii;
+    const float* g = L.gout + 5 * ii;
     const float g0 = g[0];
-    float kb = 0.f, pb = g[1], rb = g[2];
+    float kb = g[3], pb = g[1], rb = g[2];
     if (!(S.flags & SEB_FLAG_OBSTACLE)) {
       const float sp = S.pitch > 0.f ? 1.f : (S.pitch < 0.f ? -1.f : 0.f);
       const float sr = S.roll > 0.f ? 1.f : (S.roll < 0.f ? -1.f : 0.f);
-      kb += g[3] * L.w0 / L.kappa_max;
-      pb += g[3] * L.w1 * sp / L.phi_x_max;
-      rb += g[3] * L.w2 * sr / L.phi_y_max;
+      kb += g[4] * L.w0 / L.kappa_max;
+      pb += g[4] * L.w1 * sp / L.phi_x_max;
+      rb += g[4] * L.w2 * sr / L.phi_y_max;
     }
     const float* n = S.n;
     const float uz = n[0] * s - n[1] * c;

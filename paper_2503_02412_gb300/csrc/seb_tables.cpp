@@ -123,10 +123,15 @@ int build_tables(const seb_params& p, Tables* T, int32_t* total_runs) {
   }
   T->rx = rx;
   T->ry = ry;
-  if (kTileW + 2 * rx + 1 > 1024 || kTileH + 2 * ry > 1024) {
-    set_error("footprint reach too large for the staged tile");
-    return SEB_ERR_BAD_SHAPE;
-  }
+  const int64_t nr2 = (int64_t)nmax * (rx > ry ? rx : ry);
+  T->narrow = nr2 * nr2 < ((int64_t)1 << 31) ? 1 : 0;
+  // The staged tile of every layout (plus the row flags) must fit in 227 KB of shared memory.
+  for (int lg = 1; lg <= 5; lg += 2)
+    if (stage_h(lg, ry) > kMaxStageRows ||
+        ((size_t)stage_w(lg, rx) * stage_h(lg, ry) + kMaxStageRows) * sizeof(float) > 227 * 1024) {
+      set_error("footprint reach too large for the staged tile");
+      return SEB_ERR_BAD_SHAPE;
+    }
   if (total_runs) *total_runs = nr;
   return SEB_OK;
 }

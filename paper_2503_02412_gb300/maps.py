@@ -31,7 +31,7 @@ class SebParams:
     n_min: int = 0
     elev_dtype: torch.dtype = torch.float32
     precision: str = "plain"  # "plain" | "compensated"
-    gap_fp64: float = 1e-6
+    gap_fp64: float = 1e-2
 
     def c(self) -> abi.seb_params:
         p = abi.seb_params()

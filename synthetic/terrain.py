@@ -92,13 +92,16 @@ def _nan_discs(rng, z, res, frac=0.05):
     ny, nx = z.shape
     mask = np.zeros_like(z, dtype=bool)
     target = frac * nx * ny
-    while mask.sum() < target:
+    count = 0
+    while count < target:
         r = rng.uniform(0.1, 0.5) / res
         cx, cy = rng.uniform(0, nx), rng.uniform(0, ny)
         x0, x1 = max(0, int(cx - r) - 1), min(nx, int(cx + r) + 2)
         y0, y1 = max(0, int(cy - r) - 1), min(ny, int(cy + r) + 2)
         yy, xx = np.mgrid[y0:y1, x0:x1]
-        mask[y0:y1, x0:x1] |= (xx + 0.5 - cx) ** 2 + (yy + 0.5 - cy) ** 2 <= r * r
+        disc = (xx + 0.5 - cx) ** 2 + (yy + 0.5 - cy) ** 2 <= r * r
+        count += int((disc & ~mask[y0:y1, x0:x1]).sum())
+        mask[y0:y1, x0:x1] |= disc
     z = z.copy()
     z[mask] = np.nan
     return z

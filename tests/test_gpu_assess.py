@@ -1,0 +1,203 @@
+"""GPU parity of the SE(2) grid assessment (Algorithm 1 for every cell and yaw bin) against
+the FP64 oracle, through the C ABI.  Sizes: the small map and the full 400 x 400 x 72 map
+(both complete, element by element), plus ragged, degenerate and rolling cases."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synthetic import bumpy_plane, fractal_steps_nan, fractal_world, shift_sequence, tilted_plane
+
+from .parity import compare, grid_to_rows
+
+pytestmark = pytest.mark.gpu
+
+C1 = dict(nx=100, ny=100, n_yaw=36, res=0.1, length=0.6, width=0.4)
+C2 = dict(nx=400, ny=400, n_yaw=72, res=0.05, length=0.9, width=0.6)
+
+
+@pytest.fixture(scope="module")
+def seb():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2503_02412_gb300 as seb
+
+    assert torch.cuda.is_available()
+    return seb
+
+
+def run_map(seb, cfg, elev, origin=(0, 0), **kw):
+    m = seb.SebMap(seb.SebParams(**cfg, **kw))
+    dt = kw.get("elev_dtype", torch.float32)
+    m.update(torch.from_numpy(np.ascontiguousarray(elev)).to("cuda", dtype=dt), origin)
+    out, fl = m.outputs()
+    counters = m.check()
+    return m, out.cpu().numpy(), fl.cpu().numpy(), counters
+
+
+def oracle_grid(cfg, elev, origin=(0, 0), **kw):
+    return oracle.assess_grid(oracle.OracleParams(**cfg, **kw), np.asarray(elev, np.float64), origin, with_gap=True)
+
+
+def check(out, fl, ref, label):
+    o, f = grid_to_rows(out, fl)
+    r, rf, g = grid_to_rows(*ref)
+    return compare(o, f, r, rf, label=label, gap=g)
+
+
+def test_small_map_every_cell(seb):
+    e = bumpy_plane(0)
+    _, out, fl, _ = run_map(seb, C1, e, (17, -4))
+    s = check(out, fl, oracle_grid(C1, e, (17, -4)), "c1")
+    assert s["assessed"] > 0.95 * s["n"]
+
+
+def test_full_map_every_cell(seb):
+    e = fractal_steps_nan(0)
+    _, out, fl, (n64, ndeg) = run_map(seb, C2, e)
+    s = check(out, fl, oracle_grid(C2, e), "c2")
+    assert s["assessed"] > 0.8 * s["n"]
+    assert ((fl & 1) != 0).mean() > 0.01  # the NaN blobs produce unknown cells
+
+
+@pytest.mark.parametrize("cfg", [C1, dict(C2, nx=96, ny=96)])
+@pytest.mark.parametrize("ab", [(0.2, -0.1), (-0.25, 0.05)])
+def test_tilted_plane_closed_form(seb, cfg, ab):
+    a, b = ab
+    nx, ny = cfg["nx"], cfg["ny"]
+    e = tilted_plane(nx, ny, cfg["res"], a, b, 0.4, (3, 9)).astype(np.float32)
+    _, out, fl, _ = run_map(seb, cfg, e, (3, 9))
+    K = cfg["n_yaw"]
+    th = 2 * np.pi * np.arange(K) / K
+    p = a * np.cos(th) + b * np.sin(th)
+    q = b * np.cos(th) - a * np.sin(th)
+    pitch = np.arcsin(p / np.sqrt((1 + q * q) * (1 + p * p + q * q)))
+    roll = np.arctan(q)
+    R = 12
+    sl = (slice(None), slice(R, ny - R), slice(R, nx - R))
+    assert np.abs(out[1][sl] - pitch[:, None, None]).max() < 2e-5
+    assert np.abs(out[2][sl] - roll[:, None, None]).max() < 2e-5
+    assert np.abs(out[3][sl]).max() < 1e-6
+    xs = (3 + np.arange(nx) + 0.5) * cfg["res"]
+    ys = (9 + np.arange(ny) + 0.5) * cfg["res"]
+    zc = a * xs[None, :] + b * ys[:, None] + 0.4
+    assert np.abs(out[0][sl] - zc[None, R:-R, R:-R]).max() < 1e-5
+
+
+def test_flat_ground(seb):
+    e = np.full((64, 64), 1.25, np.float32)
+    _, out, fl, _ = run_map(seb, dict(C1, nx=64, ny=64), e)
+    sl = (slice(None), slice(4, 60), slice(4, 60))
+    assert (out[1][sl] == 0).all() and (out[2][sl] == 0).all() and (out[3][sl] == 0).all()
+    assert (out[4][sl] == 0).all() and (out[0][sl] == 1.25).all()
+
+
+def test_yaw_plus_pi_is_exact_negation(seb):
+    e = fractal_steps_nan(5, 160, 160)
+    _, out, fl, _ = run_map(seb, dict(C2, nx=160, ny=160), e)
+    h = 36
+    a, b = out[:, :h], out[:, h:]
+    both = np.isfinite(a[1])
+    assert np.array_equal(a[0].view(np.uint32), b[0].view(np.uint32))
+    assert np.array_equal(a[3].view(np.uint32), b[3].view(np.uint32))
+    assert np.array_equal(a[4].view(np.uint32), b[4].view(np.uint32))
+    assert np.array_equal(a[1][both], -b[1][both]) and np.array_equal(a[2][both], -b[2][both])
+    assert np.array_equal(fl[:h], fl[h:])
+
+
+def test_offset_invariance(seb):
+    e = bumpy_plane(2, 80, 80)
+    _, o1, f1, _ = run_map(seb, dict(C1, nx=80, ny=80), e)
+    _, o2, f2, _ = run_map(seb, dict(C1, nx=80, ny=80), e + np.float32(2.0))
+    ok = np.isfinite(o1[0])
+    assert np.abs(o2[0][ok] - o1[0][ok] - 2.0).max() < 1e-5
+    for ch in (1, 2, 3, 4):
+        assert np.abs(o2[ch][ok] - o1[ch][ok]).max() < 1e-5
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (37, 53), (5, 300), (300, 7), (33, 33)])
+def test_ragged_and_tiny_maps(seb, shape):
+    ny, nx = shape
+    e = fractal_steps_nan(11, nx, ny, nan_frac=0.03) if min(shape) > 4 else np.zeros(shape, np.float32)
+    cfg = dict(C2, nx=nx, ny=ny)
+    _, out, fl, _ = run_map(seb, cfg, e)
+    check(out, fl, oracle_grid(cfg, e), f"ragged {shape}")
+
+
+def test_all_unknown_map(seb):
+    e = np.full((40, 50), np.nan, np.float32)
+    _, out, fl, _ = run_map(seb, dict(C1, nx=50, ny=40), e)
+    assert (fl == 3).all() and (out[4] == 1).all() and np.isnan(out[:4]).all()
+
+
+@pytest.mark.parametrize("extra", [dict(n_yaw=2), dict(shape="ellipse"), dict(n_min=5), dict(n_yaw=8, length=1.5)])
+def test_parameter_variants(seb, extra):
+    cfg = dict(C1, nx=72, ny=56)
+    cfg.update(extra)
+    e = fractal_steps_nan(7, 72, 56, res=0.1)
+    _, out, fl, _ = run_map(seb, cfg, e)
+    check(out, fl, oracle_grid(cfg, e), str(extra))
+
+
+def test_rolling_window_bit_identical_to_rebuild(seb):
+    """Sec. V-A: the window follows the robot; after 50 moves of 10 cells in random
+    directions the ring-buffered map equals a fresh rebuild of the final window, bit for bit,
+    and a sample of its cells equals the oracle."""
+    world = fractal_world(1, 1100)
+    tw = torch.from_numpy(world).cuda()
+    p = seb.SebParams(**C2)
+    o = [350, 350]
+    win = lambda o: tw[o[1]:o[1] + 400, o[0]:o[0] + 400].contiguous()  # noqa: E731
+    m = seb.SebMap(p)
+    m.update(win(o), tuple(o))
+    cells = 0
+    for dx, dy in shift_sequence(2, 50):
+        o = [min(max(o[0] + dx, 0), 700), min(max(o[1] + dy, 0), 700)]
+        m.shift(win(o), tuple(o))
+        cells += m.view().last_cells
+    assert 0 < cells < 50 * 400 * 400 * 72
+    v = m.view()
+    assert (v.origin_i, v.origin_j) == tuple(o)
+    ro, rf = m.outputs()
+    full = seb.SebMap(p)
+    full.update(win(o), tuple(o))
+    fo, ff = full.outputs()
+    assert torch.equal(ro.view(torch.int32), fo.view(torch.int32))
+    assert torch.equal(rf, ff)
+    m.check()
+    # oracle on a sample of the final window
+    e = world[o[1]:o[1] + 400, o[0]:o[0] + 400]
+    rng = np.random.default_rng(0)
+    cells = np.stack([rng.integers(0, 400, 50000), rng.integers(0, 400, 50000), rng.integers(0, 72, 50000)], 1)
+    ref, rfl, gap = oracle.assess_cells(oracle.OracleParams(**C2), e.astype(np.float64), cells.astype(np.int32), tuple(o))
+    g = ro.cpu().numpy()[:, cells[:, 2], cells[:, 1], cells[:, 0]].T
+    gf = rf.cpu().numpy()[cells[:, 2], cells[:, 1], cells[:, 0]]
+    compare(g, gf, ref, rfl, label="rolling sample", gap=gap)
+
+
+@pytest.mark.parametrize("move", [(0, 0), (1, 0), (0, -1), (-7, 13), (399, 0), (400, 5), (-1000, 2000)])
+def test_shift_edge_moves(seb, move):
+    world = fractal_world(3, 1400)
+    tw = torch.from_numpy(world).cuda()
+    p = seb.SebParams(**C2)
+    o0 = [500, 500]
+    win = lambda o: tw[o[1]:o[1] + 400, o[0]:o[0] + 400].contiguous()  # noqa: E731
+    m = seb.SebMap(p)
+    m.update(win(o0), tuple(o0))
+    o1 = [o0[0] + move[0], o0[1] + move[1]]
+    o1 = [min(max(o1[0], 0), 1000), min(max(o1[1], 0), 1000)]
+    m.shift(win(o1), tuple(o1))
+    full = seb.SebMap(p)
+    full.update(win(o1), tuple(o1))
+    a, af = m.outputs()
+    b, bf = full.outputs()
+    assert torch.equal(a.view(torch.int32), b.view(torch.int32)) and torch.equal(af, bf)
+
+
+def test_host_pointer_rejected(seb):
+    m = seb.SebMap(seb.SebParams(**C1))
+    host = torch.zeros(100, 100)
+    with pytest.raises(seb.abi.SebError) as ei:
+        seb.abi.seb_map_update(m.handle, host.data_ptr(), 0, 0)
+    assert ei.value.status == seb.abi.SEB_ERR_INVALID_ARG
