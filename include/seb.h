@@ -202,6 +202,28 @@ int seb_query_poses_backward(const seb_params* p, const void* elev_dev, int64_t 
                              const float* grad_out_dev, float* grad_pose_dev, int64_t n,
                              seb_stream_t stream);
 
+/*
+ * Allocation-free pose query: the forward and the backward of seb_query_poses /
+ * seb_query_poses_backward in one call, for callers that cannot allocate device memory
+ * (a real-time loop held to a fixed memory budget, or an embedding host whose allocator the
+ * library may not touch).  The paper has no counterpart: this is a packaging of the query
+ * above.  The per-pose state passed from the forward to the backward lives in a file-scope
+ * device array of SEB_NOALLOC_MAX_POSES records (4 MiB) instead of a caller buffer; every GPU
+ * that loads the library keeps that array until the process exits.
+ *   poses_dev [n][3], grad_out_dev [n][SEB_N_CH] (inputs); out_dev [n][SEB_N_CH],
+ *   flags_dev [n], grad_pose_dev [n][3] (outputs, caller-owned).
+ * n > SEB_NOALLOC_MAX_POSES returns SEB_ERR_INVALID_ARG with a message naming the limit.
+ * Calls no allocating routine.  All calls share the array: calls whose kernels overlap on the
+ * GPU (unordered streams) race on it; calls on one stream are safe.  Nothing in it needs
+ * clearing: the forward writes every record the backward reads.  The first call on a device
+ * looks the array's address up with that device current; make it before any stream capture.
+ */
+#define SEB_NOALLOC_MAX_POSES 65536
+int seb_query_poses_grad_noalloc(const seb_params* p, const void* elev_dev, int64_t origin_i,
+                                 int64_t origin_j, const float* poses_dev, int64_t n,
+                                 const float* grad_out_dev, float* out_dev, uint8_t* flags_dev,
+                                 float* grad_pose_dev, seb_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,6 +26,7 @@ SEB_PLAIN_F32, SEB_COMPENSATED = 0, 1
 SEB_FLAG_UNKNOWN, SEB_FLAG_OBSTACLE, SEB_FLAG_DEGENERATE, SEB_FLAG_FP64 = 1, 2, 4, 8
 SEB_N_CH = 5
 SEB_QUERY_SAVED = 16
+SEB_NOALLOC_MAX_POSES = 65536
 
 # Every extern "C" symbol declared in include/seb.h.
 EXPORTS = (
@@ -44,6 +45,7 @@ EXPORTS = (
     "seb_map_check",
     "seb_query_poses",
     "seb_query_poses_backward",
+    "seb_query_poses_grad_noalloc",
 )
 
 
@@ -123,6 +125,7 @@ def load():
             "seb_map_check": (ctypes.c_int, [vp, i32, i64p, i64p]),
             "seb_query_poses": (ctypes.c_int, [P, vp, i64, i64, vp, i64, vp, vp, vp, vp]),
             "seb_query_poses_backward": (ctypes.c_int, [P, vp, i64, i64, vp, vp, vp, vp, i64, vp]),
+            "seb_query_poses_grad_noalloc": (ctypes.c_int, [P, vp, i64, i64, vp, i64, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -222,3 +225,10 @@ def seb_query_poses_backward(p: seb_params, elev_ptr, origin_i, origin_j, poses_
     _check(load().seb_query_poses_backward(ctypes.byref(p), elev_ptr, origin_i, origin_j, poses_ptr,
                                            saved_ptr, grad_out_ptr, grad_pose_ptr, n, stream))
 
+
+def seb_query_poses_grad_noalloc(p: seb_params, elev_ptr, origin_i, origin_j, poses_ptr, n, grad_out_ptr, out_ptr,
+                                 flags_ptr, grad_pose_ptr, stream=0) -> None:
+    """Forward + backward of the pose query without any device allocation (saved state in the
+    library's own device array; at most SEB_NOALLOC_MAX_POSES poses per call)."""
+    _check(load().seb_query_poses_grad_noalloc(ctypes.byref(p), elev_ptr, origin_i, origin_j, poses_ptr, n,
+                                               grad_out_ptr, out_ptr, flags_ptr, grad_pose_ptr, stream))
