@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-rebuild", action="store_true",
+                    help="only run three full rebuilds of the map (a short program for ncu)")
     return ap.parse_args()
 
 
@@ -187,8 +189,25 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def profile_rebuild():
+    """Three rebuilds of the 400x400x72 map and nothing else: the program ncu captures."""
+    import torch
+
+    import paper_2503_02412_gb300 as seb
+    from synthetic import fractal_steps_nan
+
+    e = torch.from_numpy(fractal_steps_nan(0)).cuda()
+    m = seb.SebMap(seb.SebParams(nx=NX, ny=NY, n_yaw=K, res=RES, length=LENGTH, width=WIDTH))
+    for _ in range(3):
+        m.update(e)
+    m.check()
+    torch.cuda.synchronize()
+
+
 def main():
     args = parse()
+    if args.profile_rebuild:
+        return profile_rebuild()
     if args.impl == "reference":
         return run_reference(args)
     rank, local_rank, world_size = dist_env()

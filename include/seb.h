@@ -65,6 +65,7 @@ extern "C" {
 #define SEB_FLAG_OBSTACLE 2   /* risk == 1 (an explicit obstacle, Algorithm 1) */
 #define SEB_FLAG_DEGENERATE 4 /* normal undefined: eigen-gap ~ 0, n_z <= 1e-6 or yaw || normal */
 #define SEB_FLAG_FP64 8       /* eigen-solve redone in FP64 (small relative eigen-gap) */
+#define SEB_FLAG_SURROGATE 16 /* value predicted by the learned surrogate (seb_sur_infer) */
 
 #define SEB_N_CH 5 /* z, pitch, roll, roughness, risk */
 
@@ -201,6 +202,80 @@ int seb_query_poses_backward(const seb_params* p, const void* elev_dev, int64_t 
                              int64_t origin_j, const float* poses_dev, const float* saved_dev,
                              const float* grad_out_dev, float* grad_pose_dev, int64_t n,
                              seb_stream_t stream);
+
+/*
+ * Learned surrogate (not in the paper, which names learned traversability as less reliable
+ * than geometry, Sec. II-A): a BF16 convolutional network predicting, per cell and yaw pair,
+ * (z - z_cell, pitch, roll, risk) of the assessment above from an elevation patch.  Slope
+ * features (central differences) -> 4 x [3x3 conv, 32 channels, dilations 1, 2, 4, 8, ReLU]
+ * -> 1x1 head to 4 x n_yaw/2 outputs; receptive field 31 cells (a 48 x 48 crop, the centre
+ * of a 64 x 64 patch, gives the 16 x 16 centre cells).  Weights and stored activations BF16,
+ * accumulation and gradients FP32, FP32 master weights with Adam.  Trained on the GPU on
+ * patches the exact kernel labels; run fully convolutionally over a map with the exact kernel
+ * as fallback near unknown cells, step edges and the map border.
+ *
+ * The handle lives on caller workspace (>= seb_sur_workspace_bytes, 256-byte aligned) sized
+ * for training batches of up to max_batch patches and for inference on a p->nx x p->ny map;
+ * p gives the exact assessment the network imitates (p->elev_dtype must be SEB_F32).
+ * seb_sur_view reports byte offsets of the parts of the workspace (weights for save / load,
+ * batch buffers, activations) so a caller can inspect or checkpoint them.
+ */
+typedef struct seb_sur seb_sur;
+typedef struct {
+  int64_t n_params;           /* FP32 master parameters */
+  int32_t n_out;              /* 2 * n_yaw head outputs */
+  int32_t max_batch;
+  size_t master, adam_m, adam_v, grad, weights_bf16;  /* [n_params] each */
+  size_t features;            /* [max_batch][46][46][2] BF16 */
+  size_t labels;              /* [max_batch][16][16][n_out] FP32 (NaN = no label) */
+  size_t act[4];              /* [max_batch][side][side][32] BF16, sides 44, 40, 32, 16 */
+  size_t dact[4];             /* FP32 gradients of the same */
+  size_t pred, dpred;         /* [max_batch][16][16][n_out] FP32 */
+  size_t map_features, map_act[4], mask, tiles, partials, loss_partials, totals;
+  int64_t off_w[4], off_b[4], off_wh, off_bh;  /* parameter offsets (elements) */
+} seb_sur_view;
+
+size_t seb_sur_workspace_bytes(const seb_params* p, int32_t max_batch);
+int seb_sur_create(const seb_params* p, int32_t max_batch, void* workspace_dev, size_t bytes,
+                   seb_stream_t stream, seb_sur** out);
+int seb_sur_destroy(seb_sur* h);
+int seb_sur_set_stream(seb_sur* h, seb_stream_t stream);
+int seb_sur_view_get(const seb_sur* h, seb_sur_view* v);
+/* Engine of the 32 -> 32 convolutions: SEB_SUR_TCGEN05 (default; tensor cores: tcgen05.mma
+ * implicit GEMM, M = 128 pixels, N = 32, K = 288, FP32 accumulation in tensor memory) or
+ * SEB_SUR_SIMT (FP32 CUDA cores).  Backward passes always run on the CUDA cores. */
+#define SEB_SUR_SIMT 0
+#define SEB_SUR_TCGEN05 1
+int seb_sur_set_engine(seb_sur* h, int32_t engine);
+/* He-normal weights from a counter-based generator (SplitMix64 + Box-Muller), zero Adam state. */
+int seb_sur_init(seb_sur* h, uint64_t seed);
+/*
+ * Writes training patches [offset, offset + n) of the batch: centres_dev [n][2] (cx, cy) name
+ * 48 x 48 crops [cx-24, cx+24) x [cy-24, cy+24) of elev_dev [ny][nx]; labels come from
+ * exact_dev, the exact assessment of that elevation in logical order [5][n_yaw][ny][nx]
+ * (seb_map_copy_out).  Crops outside the map raise the device error word.
+ */
+int seb_sur_gather(seb_sur* h, const float* elev_dev, const float* exact_dev, int32_t nx, int32_t ny,
+                   const int32_t* centres_dev, int32_t n, int32_t offset);
+/* Forward, mean squared error over the finite labels, backward and one Adam step (step >= 1)
+ * on the first `batch` patches; loss_dev (may be NULL) receives the loss. */
+int seb_sur_train_step(seb_sur* h, int32_t batch, float lr, int32_t step, float* loss_dev);
+/* Forward only (evaluation) into the pred buffer. */
+int seb_sur_forward(seb_sur* h, int32_t batch);
+/*
+ * Inference on a p->nx x p->ny map: writes out_dev [5][n_yaw][ny][nx] and flags_dev like a
+ * map (roughness is not predicted: NaN, flag SEB_FLAG_SURROGATE) for the cells at least 16
+ * from the border; mask_dev [ny][nx] (may be NULL) receives the fallback mask (a NaN or a
+ * 4-neighbour step above `step` metres within Chebyshev distance `radius`, or the border);
+ * with exact_fallback != 0 the exact kernel then overwrites every masked cell.
+ */
+int seb_sur_infer(seb_sur* h, const float* elev_dev, float step, int32_t radius, int32_t exact_fallback,
+                  float* out_dev, uint8_t* flags_dev, uint8_t* mask_dev);
+/* Terrain of the small-map recipe on the GPU (training data): per world 36 parameters
+ * (tan slope, azimuth, noise sigma, unused, then (amplitude, sigma, cx, cy) x 8 bumps); the
+ * noise is N(0, sigma) from a counter-based generator seeded by seed.  out_dev [n][ny][nx]. */
+int seb_terrain_bumpy(const float* params_dev, int32_t n, int32_t nx, int32_t ny, float res, uint64_t seed,
+                      float* out_dev, seb_stream_t stream);
 
 /*
  * Allocation-free pose query: the forward and the backward of seb_query_poses /

@@ -24,6 +24,8 @@ SEB_RECT, SEB_ELLIPSE = 0, 1
 SEB_F32, SEB_BF16, SEB_F16 = 0, 1, 2
 SEB_PLAIN_F32, SEB_COMPENSATED = 0, 1
 SEB_FLAG_UNKNOWN, SEB_FLAG_OBSTACLE, SEB_FLAG_DEGENERATE, SEB_FLAG_FP64 = 1, 2, 4, 8
+SEB_FLAG_SURROGATE = 16
+SEB_SUR_SIMT, SEB_SUR_TCGEN05 = 0, 1
 SEB_N_CH = 5
 SEB_QUERY_SAVED = 16
 SEB_NOALLOC_MAX_POSES = 65536
@@ -46,6 +48,18 @@ EXPORTS = (
     "seb_query_poses",
     "seb_query_poses_backward",
     "seb_query_poses_grad_noalloc",
+    "seb_sur_workspace_bytes",
+    "seb_sur_create",
+    "seb_sur_destroy",
+    "seb_sur_set_stream",
+    "seb_sur_view_get",
+    "seb_sur_set_engine",
+    "seb_sur_init",
+    "seb_sur_gather",
+    "seb_sur_train_step",
+    "seb_sur_forward",
+    "seb_sur_infer",
+    "seb_terrain_bumpy",
 )
 
 
@@ -89,6 +103,36 @@ class seb_view(ctypes.Structure):
     ]
 
 
+class seb_sur_view(ctypes.Structure):
+    _fields_ = [
+        ("n_params", ctypes.c_int64),
+        ("n_out", ctypes.c_int32),
+        ("max_batch", ctypes.c_int32),
+        ("master", ctypes.c_size_t),
+        ("adam_m", ctypes.c_size_t),
+        ("adam_v", ctypes.c_size_t),
+        ("grad", ctypes.c_size_t),
+        ("weights_bf16", ctypes.c_size_t),
+        ("features", ctypes.c_size_t),
+        ("labels", ctypes.c_size_t),
+        ("act", ctypes.c_size_t * 4),
+        ("dact", ctypes.c_size_t * 4),
+        ("pred", ctypes.c_size_t),
+        ("dpred", ctypes.c_size_t),
+        ("map_features", ctypes.c_size_t),
+        ("map_act", ctypes.c_size_t * 4),
+        ("mask", ctypes.c_size_t),
+        ("tiles", ctypes.c_size_t),
+        ("partials", ctypes.c_size_t),
+        ("loss_partials", ctypes.c_size_t),
+        ("totals", ctypes.c_size_t),
+        ("off_w", ctypes.c_int64 * 4),
+        ("off_b", ctypes.c_int64 * 4),
+        ("off_wh", ctypes.c_int64),
+        ("off_bh", ctypes.c_int64),
+    ]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -126,6 +170,18 @@ def load():
             "seb_query_poses": (ctypes.c_int, [P, vp, i64, i64, vp, i64, vp, vp, vp, vp]),
             "seb_query_poses_backward": (ctypes.c_int, [P, vp, i64, i64, vp, vp, vp, vp, i64, vp]),
             "seb_query_poses_grad_noalloc": (ctypes.c_int, [P, vp, i64, i64, vp, i64, vp, vp, vp, vp, vp]),
+            "seb_sur_workspace_bytes": (sz, [P, i32]),
+            "seb_sur_create": (ctypes.c_int, [P, i32, vp, sz, vp, ctypes.POINTER(vp)]),
+            "seb_sur_destroy": (ctypes.c_int, [vp]),
+            "seb_sur_set_stream": (ctypes.c_int, [vp, vp]),
+            "seb_sur_view_get": (ctypes.c_int, [vp, ctypes.POINTER(seb_sur_view)]),
+            "seb_sur_set_engine": (ctypes.c_int, [vp, i32]),
+            "seb_sur_init": (ctypes.c_int, [vp, ctypes.c_uint64]),
+            "seb_sur_gather": (ctypes.c_int, [vp, vp, vp, i32, i32, vp, i32, i32]),
+            "seb_sur_train_step": (ctypes.c_int, [vp, i32, ctypes.c_float, i32, vp]),
+            "seb_sur_forward": (ctypes.c_int, [vp, i32]),
+            "seb_sur_infer": (ctypes.c_int, [vp, vp, ctypes.c_float, i32, i32, vp, vp, vp]),
+            "seb_terrain_bumpy": (ctypes.c_int, [vp, i32, i32, i32, ctypes.c_float, ctypes.c_uint64, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -232,3 +288,55 @@ def seb_query_poses_grad_noalloc(p: seb_params, elev_ptr, origin_i, origin_j, po
     library's own device array; at most SEB_NOALLOC_MAX_POSES poses per call)."""
     _check(load().seb_query_poses_grad_noalloc(ctypes.byref(p), elev_ptr, origin_i, origin_j, poses_ptr, n,
                                                grad_out_ptr, out_ptr, flags_ptr, grad_pose_ptr, stream))
+
+
+def seb_sur_workspace_bytes(p: seb_params, max_batch: int) -> int:
+    return int(load().seb_sur_workspace_bytes(ctypes.byref(p), max_batch))
+
+
+def seb_sur_create(p: seb_params, max_batch: int, workspace_ptr: int, nbytes: int, stream: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(load().seb_sur_create(ctypes.byref(p), max_batch, workspace_ptr, nbytes, stream, ctypes.byref(h)))
+    return h.value
+
+
+def seb_sur_destroy(handle: int) -> None:
+    _check(load().seb_sur_destroy(handle))
+
+
+def seb_sur_set_stream(handle: int, stream: int) -> None:
+    _check(load().seb_sur_set_stream(handle, stream))
+
+
+def seb_sur_view_get(handle: int) -> seb_sur_view:
+    v = seb_sur_view()
+    _check(load().seb_sur_view_get(handle, ctypes.byref(v)))
+    return v
+
+
+def seb_sur_set_engine(handle: int, engine: int) -> None:
+    _check(load().seb_sur_set_engine(handle, engine))
+
+
+def seb_sur_init(handle: int, seed: int) -> None:
+    _check(load().seb_sur_init(handle, seed))
+
+
+def seb_sur_gather(handle, elev_ptr, exact_ptr, nx, ny, centres_ptr, n, offset) -> None:
+    _check(load().seb_sur_gather(handle, elev_ptr, exact_ptr, nx, ny, centres_ptr, n, offset))
+
+
+def seb_sur_train_step(handle, batch, lr, step, loss_ptr=0) -> None:
+    _check(load().seb_sur_train_step(handle, batch, lr, step, loss_ptr))
+
+
+def seb_sur_forward(handle, batch) -> None:
+    _check(load().seb_sur_forward(handle, batch))
+
+
+def seb_sur_infer(handle, elev_ptr, step, radius, exact_fallback, out_ptr, flags_ptr, mask_ptr=0) -> None:
+    _check(load().seb_sur_infer(handle, elev_ptr, step, radius, exact_fallback, out_ptr, flags_ptr, mask_ptr))
+
+
+def seb_terrain_bumpy(params_ptr, n, nx, ny, res, seed, out_ptr, stream=0) -> None:
+    _check(load().seb_terrain_bumpy(params_ptr, n, nx, ny, res, seed, out_ptr, stream))

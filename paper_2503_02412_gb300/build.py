@@ -33,8 +33,9 @@ def _headers():
 
 
 def _flags(extra=()):
+    defs = [f"-D{d}" for d in os.environ.get("SEB_DEFINES", "").split() if d]
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
-                   "--expt-relaxed-constexpr", *extra]
+                   "--expt-relaxed-constexpr", *defs, *extra]
 
 
 def _compile(src, extra):

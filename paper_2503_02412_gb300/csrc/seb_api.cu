@@ -55,33 +55,37 @@ static int fail(seb_map* m, int code, const char* msg) {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+void launch_defaults(const seb_params& p, const Tables& T, Launch* L) {
+  memset(L, 0, sizeof(*L));
+  L->nx = p.nx;
+  L->ny = p.ny;
+  L->plane = (int64_t)p.nx * p.ny;
+  L->n_yaw = p.n_yaw;
+  L->res = p.res;
+  L->kappa_max = p.kappa_max;
+  L->phi_x_max = p.phi_x_max;
+  L->phi_y_max = p.phi_y_max;
+  L->w0 = p.w[0];
+  L->w1 = p.w[1];
+  L->w2 = p.w[2];
+  L->gap_fp64 = p.gap_fp64;
+  L->narrow_moments = T.narrow;
+}
+
 static Launch base_launch(const seb_map* m, const void* elev) {
   Launch L;
-  memset(&L, 0, sizeof(L));
+  launch_defaults(m->p, m->T, &L);
   L.elev = elev;
-  L.nx = m->p.nx;
-  L.ny = m->p.ny;
   L.ring_x = m->ring_x;
   L.ring_y = m->ring_y;
   L.out = m->out;
   L.flags = m->flags;
-  L.plane = (int64_t)m->p.nx * m->p.ny;
-  L.n_yaw = m->p.n_yaw;
-  L.res = m->p.res;
-  L.kappa_max = m->p.kappa_max;
-  L.phi_x_max = m->p.phi_x_max;
-  L.phi_y_max = m->p.phi_y_max;
-  L.w0 = m->p.w[0];
-  L.w1 = m->p.w[1];
-  L.w2 = m->p.w[2];
-  L.gap_fp64 = m->p.gap_fp64;
-  L.narrow_moments = m->T.narrow;
   L.err = &m->ctl->err;
   L.counters = &m->ctl->n_fp64;
   return L;
 }
 
-static void push_rect(Launch& L, int x0, int y0, int w, int h, int lg) {
+void push_rect(Launch& L, int x0, int y0, int w, int h, int lg) {
   if (w <= 0 || h <= 0) return;
   const int i = L.n_rects++;
   L.rects[i] = Rect{x0, y0, w, h, lg};
@@ -92,7 +96,7 @@ static void push_rect(Launch& L, int x0, int y0, int w, int h, int lg) {
 
 // A rectangle of cells to recompute, split so that no tile is mostly empty: whole 32 x 32
 // tiles, a right remainder in 8-wide tiles and a bottom remainder in 8-tall tiles.
-static void add_rect(Launch& L, int x0, int y0, int w, int h) {
+void launch_add_rect(Launch& L, int x0, int y0, int w, int h) {
   if (w <= 0 || h <= 0) return;
   const int wm = w >= 32 ? w - w % 32 : 0, hm = h >= 32 ? h - h % 32 : 0;
   if (wm && hm) {
@@ -124,6 +128,10 @@ static int check_elev(seb_map* m, const void* elev) {
     return fail(m, SEB_ERR_INVALID_ARG, "elevation must be device memory");
   return SEB_OK;
 }
+
+// One rectangle in whole 32 x 32 tiles (the last row/column ragged), so that tile t of the
+// launch is tile (t % tiles_x, t / tiles_x) of the rectangle's 32 x 32 grid.
+void launch_add_tiles(Launch& L, int x0, int y0, int w, int h) { push_rect(L, x0, y0, w, h, 3); }
 
 }  // namespace seb
 
@@ -220,7 +228,7 @@ int seb_map_update(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
   if (rc) return rc;
   m->ring_x = m->ring_y = 0;
   Launch L = base_launch(m, elev);
-  add_rect(L, 0, 0, m->p.nx, m->p.ny);
+  launch_add_rect(L, 0, 0, m->p.nx, m->p.ny);
   cudaError_t e = launch_assess(m->T, L, m->p.elev_dtype, m->p.precision, m->stream);
   if (e != cudaSuccess) return cuda_fail(m, e, "assess launch");
   m->last_cells = rect_cells(L, m->p.n_yaw);
@@ -266,12 +274,12 @@ int seb_map_shift(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
   }
   Launch L = base_launch(m, elev);
   if (left + right >= nx || top + bottom >= ny) {
-    add_rect(L, 0, 0, nx, ny);
+    launch_add_rect(L, 0, 0, nx, ny);
   } else {
-    add_rect(L, 0, 0, left, ny);
-    add_rect(L, nx - right, 0, right, ny);
-    add_rect(L, left, 0, nx - left - right, top);
-    add_rect(L, left, ny - bottom, nx - left - right, bottom);
+    launch_add_rect(L, 0, 0, left, ny);
+    launch_add_rect(L, nx - right, 0, right, ny);
+    launch_add_rect(L, left, 0, nx - left - right, top);
+    launch_add_rect(L, left, ny - bottom, nx - left - right, bottom);
   }
   cudaError_t e = launch_assess(m->T, L, m->p.elev_dtype, m->p.precision, m->stream);
   if (e != cudaSuccess) return cuda_fail(m, e, "assess launch (shift)");

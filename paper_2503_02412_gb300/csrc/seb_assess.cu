@@ -283,6 +283,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
   // Which rectangle and tile this CTA covers, and the rectangle's layout.
   const int b = blockIdx.x;
+  if (L.tile_active && !L.tile_active[b]) return;  // uniform per CTA, before any barrier
   int ri = 0;
 #pragma unroll 1
   while (ri + 1 < L.n_rects && b >= L.tile_start[ri + 1]) ++ri;
@@ -356,6 +357,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   for (int g = 0; g < kG; ++g) {
     const int c = cx + g;
     if (c >= R.x0 + R.w) break;
+    if (L.store_mask && !L.store_mask[(int64_t)cy * L.nx + c]) continue;
     const Cell o = finish_cell(mom[0] - (int)Q[0][g], mom[1] - (int)Q[1][g], mom[2] - (int)Q[2][g],
                                mom[3] - (int)Q[3][g], mom[4] - (int)Q[4][g], mom[5] - (int)Q[5][g], S0[g], S1[g],
                                S2[g], S3[g], ref[g], T.n_min[pair], ct, st, L);
@@ -379,6 +381,267 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
 }
 
+// ------------------------------------------------------------------------------------------------
+// Plain-precision kernel on packed FP32 pairs.  Each thread owns a 2 x 2 block of cells; the
+// staged tile is stored as vertical pairs (T[r][c], T[r+1][c]) so that one 8-byte shared load
+// feeds both rows of a column, and the moment updates run as FP32x2 instructions
+// (__fadd2_rn / __ffma2_rn round each half exactly like the scalar forms).  Every cell performs
+// the same operations in the same order as assess_kernel, so the results are bit-identical.
+// Alternate pair rows are skewed by one element, which keeps a half-warp (8 column pairs x 2
+// pair rows) on 32 distinct banks.
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+__device__ __forceinline__ int pair_index(int r, int c, int sw2) { return r * sw2 + c + ((r >> 1) & 1); }
+
+#ifndef SEB_ASSESS_MIN_BLOCKS
+#define SEB_ASSESS_MIN_BLOCKS 2  // CTAs per SM the register budget is sized for
+#endif
+template <typename E>
+__global__ void __launch_bounds__(kThreads, SEB_ASSESS_MIN_BLOCKS)
+    assess_kernel_x2(const __grid_constant__ Tables T, const __grid_constant__ Launch L) {
+  extern __shared__ float smem[];
+  int* rowflag = reinterpret_cast<int*>(smem);
+  float2* pt = reinterpret_cast<float2*>(smem + kMaxStageRows);  // [sh - 1][sw2] vertical pairs of heights
+  // (unknown -> 0), then the matching pairs of known weights, then per-thread missing moments
+  float2* pm = pt + (size_t)(kThreads >> 1) * 0;  // placeholder, set below once sh, sw2 are known
+  if (blockDim.x != kThreads || blockIdx.y >= (unsigned)T.n_pairs) {
+    if (threadIdx.x == 0) atomicOr(L.err, kErrLaunchShape);
+    return;
+  }
+  const int b = blockIdx.x;
+  if (L.tile_active && !L.tile_active[b]) return;  // uniform per CTA, before any barrier
+  int ri = 0;
+#pragma unroll 1
+  while (ri + 1 < L.n_rects && b >= L.tile_start[ri + 1]) ++ri;
+  const Rect R = L.rects[ri];
+  const int lg = R.log_tpr;
+  const int tw = kG << lg, th = kThreads >> lg;
+  const int t = b - L.tile_start[ri];
+  const int tx0 = R.x0 + (t % L.tiles_x[ri]) * tw;
+  const int ty0 = R.y0 + (t / L.tiles_x[ri]) * th;
+  const int rx = T.rx, ry = T.ry;
+  const int sw = tw + 2 * rx, sh = th + 2 * ry;
+  const int sw2 = sw + 1;
+
+  const int npair = (sh - 1) * sw2;
+  pm = pt + npair;
+  float2* qs = pm + npair;  // [6][kThreads] float2 per column of the thread: [g][k][tid]
+  for (int i = threadIdx.x; i < sh; i += kThreads) rowflag[i] = 0;
+  for (int i = threadIdx.x; i < 12 * kThreads; i += kThreads) qs[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const E* __restrict__ elev = static_cast<const E*>(L.elev);
+  for (int idx = threadIdx.x; idx < sw * sh; idx += kThreads) {
+    const int row = idx / sw, col = idx - row * sw;
+    const int gy = ty0 - ry + row, gx = tx0 - rx + col;
+    float v = 0.f, m = 0.f;
+    if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) {
+      const float e = to_f32<E>(elev[(int64_t)gy * L.nx + gx]);
+      if (e == e) {
+        v = e;
+        m = 1.f;
+      }
+    }
+    if (m == 0.f) rowflag[row] = 1;
+    if (row < sh - 1) {
+      const int k = pair_index(row, col, sw2);
+      pt[k].x = v;
+      pm[k].x = m;
+    }
+    if (row > 0) {
+      const int k = pair_index(row - 1, col, sw2);
+      pt[k].y = v;
+      pm[k].y = m;
+    }
+  }
+  __syncthreads();
+
+  // 2 x 2 cells per thread: column pair cp, row pair rp (see the bank note above).
+  const int cpr = (tw >> 1);                   // column pairs per row
+  const int g8 = cpr < 8 ? cpr : 8;
+  const int tid = threadIdx.x;
+  const int cp = (tid % g8) + g8 * ((tid / (2 * g8)) % (cpr / g8));
+  const int rp = ((tid / g8) & 1) + 2 * (tid / (2 * cpr));
+  const int lx = 2 * cp, ly = 2 * rp;
+  const int cx = tx0 + lx, cy = ty0 + ly;
+  if (L.store_mask) {
+    // masked-store launch: a warp without a cell to store skips the work (warp-uniform,
+    // after the last barrier)
+    int need = 0;
+    for (int h = 0; h < 2; ++h)
+      for (int g = 0; g < 2; ++g) {
+        const int c = cx + g, r = cy + h;
+        if (c < R.x0 + R.w && r < R.y0 + R.h && L.store_mask[(int64_t)r * L.nx + c]) need = 1;
+      }
+    if (!__any_sync(0xffffffffu, need)) return;
+  }
+  const int pair = blockIdx.y;
+  const int r0 = T.run_start[pair], r1 = T.run_start[pair + 1];
+  const float qnan = __int_as_float(0x7fc00000);
+  auto tile_at = [&](int row, int col) {  // staged height (row, col), NaN when unknown
+    const int k = row < sh - 1 ? pair_index(row, col, sw2) : pair_index(row - 1, col, sw2);
+    const float v = row < sh - 1 ? pt[k].x : pt[k].y, m = row < sh - 1 ? pm[k].x : pm[k].y;
+    return m != 0.f ? v : qnan;
+  };
+
+  // references: the centre height, else the first known footprint cell in run order
+  float ref[2][2];  // [col g][row h]
+#pragma unroll
+  for (int g = 0; g < 2; ++g)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float r = tile_at(ry + ly + h, rx + lx + g);
+      if (r != r) {
+        r = 0.f;
+        bool found = false;
+        for (int q = r0; q < r1 && !found; ++q) {
+          const uint32_t pk = T.runs[q];
+          const int dj = unpack(pk, 0), lo = unpack(pk, 8), hi = unpack(pk, 16);
+          for (int d = lo; d <= hi; ++d) {
+            const float v = tile_at(ry + ly + h + dj, rx + lx + g + d);
+            if (v == v) {
+              r = v;
+              found = true;
+              break;
+            }
+          }
+        }
+      }
+      ref[g][h] = r;
+    }
+  const float2 nref[2] = {f2(-ref[0][0], -ref[0][1]), f2(-ref[1][0], -ref[1][1])};
+  const float2 mref[2] = {nref[0], nref[1]};
+
+  float2 S0[2], S1[2], S2[2], S3[2];
+#pragma unroll
+  for (int g = 0; g < 2; ++g) S0[g] = S1[g] = S2[g] = S3[g] = f2(0.f, 0.f);
+  const int tq = threadIdx.x;
+  auto Qs = [&](int k, int g) -> float2& { return qs[(g * 6 + k) * kThreads + tq]; };
+  const float2 one2 = f2(1.f, 1.f);
+  for (int q = r0; q < r1; ++q) {
+    const uint32_t pk = T.runs[q];
+    const int dj = unpack(pk, 0), lo = unpack(pk, 8), hi = unpack(pk, 16);
+    const int row = ry + ly + dj;  // pair row of this thread for the run
+    const bool masked = __any_sync(0xffffffffu, rowflag[row] | rowflag[row + 1]);
+    const int base = pair_index(row, rx + lx + lo, sw2);
+    const float2* pq = pt + base;
+    const float2* pw = pm + base;
+    const int len = hi - lo + 1;
+    float2 a[2], bb[2], s3[2];
+#pragma unroll
+    for (int g = 0; g < 2; ++g) a[g] = bb[g] = s3[g] = f2(0.f, 0.f);
+    float2 di2 = f2((float)lo, (float)lo);
+    if (!masked) {
+      float2 w0 = pq[0];
+#pragma unroll 4
+      for (int i = 0; i < len; ++i) {
+        const float2 w1 = pq[i + 1];
+        float2 zp = add2(w0, nref[0]);
+        a[0] = add2(a[0], zp);
+        bb[0] = fma2(di2, zp, bb[0]);
+        s3[0] = fma2(zp, zp, s3[0]);
+        zp = add2(w1, nref[1]);
+        a[1] = add2(a[1], zp);
+        bb[1] = fma2(di2, zp, bb[1]);
+        s3[1] = fma2(zp, zp, s3[1]);
+        w0 = w1;
+        di2 = add2(di2, one2);
+      }
+    } else {
+      // unknown heights were staged as 0 with weight 0: z' = fma(-ref, m, z) is exactly
+      // z - ref for known points and 0 for unknown ones; x = 1 - m counts the missing points
+      float2 z0 = pq[0], m0 = pw[0];
+      float2 qn[2], qx[2], qxx[2];
+#pragma unroll
+      for (int g = 0; g < 2; ++g) qn[g] = qx[g] = qxx[g] = f2(0.f, 0.f);
+      const float2 neg1 = f2(-1.f, -1.f);
+#pragma unroll 2
+      for (int i = 0; i < len; ++i) {
+        const float2 z1 = pq[i + 1], m1 = pw[i + 1];
+        const float2 d2 = __fmul2_rn(di2, di2);
+        const float2 zs[2] = {z0, z1}, ms[2] = {m0, m1};
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+          const float2 zp = fma2(mref[g], ms[g], zs[g]);
+          const float2 x = fma2(neg1, ms[g], one2);
+          a[g] = add2(a[g], zp);
+          bb[g] = fma2(di2, zp, bb[g]);
+          s3[g] = fma2(zp, zp, s3[g]);
+          qn[g] = add2(qn[g], x);
+          qx[g] = fma2(di2, x, qx[g]);
+          qxx[g] = fma2(d2, x, qxx[g]);
+        }
+        z0 = z1;
+        m0 = m1;
+        di2 = add2(di2, one2);
+      }
+      const float fdj = (float)dj;
+      const float2 dj2 = f2(fdj, fdj), dj22 = f2(fdj * fdj, fdj * fdj);
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        Qs(0, g) = add2(Qs(0, g), qn[g]);
+        Qs(1, g) = add2(Qs(1, g), qx[g]);
+        Qs(2, g) = fma2(dj2, qn[g], Qs(2, g));
+        Qs(3, g) = add2(Qs(3, g), qxx[g]);
+        Qs(4, g) = fma2(dj2, qx[g], Qs(4, g));
+        Qs(5, g) = fma2(dj22, qn[g], Qs(5, g));
+      }
+    }
+    const float2 dj2 = f2((float)dj, (float)dj);
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      S0[g] = add2(S0[g], a[g]);
+      S1[g] = add2(S1[g], bb[g]);
+      S2[g] = fma2(dj2, a[g], S2[g]);
+      S3[g] = add2(S3[g], s3[g]);
+    }
+  }
+
+  const int k0 = pair, k1 = pair + T.n_pairs;
+  const float ct = T.cos_t[pair], st = T.sin_t[pair];
+  const int64_t chs = (int64_t)L.n_yaw * L.plane;
+  const int* mom = T.mom[pair];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int cyh = cy + h;
+    if (cyh >= R.y0 + R.h) break;
+    int pr = cyh + L.ring_y;
+    if (pr >= L.ny) pr -= L.ny;
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      const int c = cx + g;
+      if (c >= R.x0 + R.w) break;
+      if (L.store_mask && !L.store_mask[(int64_t)cyh * L.nx + c]) continue;
+      float qv[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) qv[k] = h ? Qs(k, g).y : Qs(k, g).x;
+      const float q0 = qv[0], q1 = qv[1], q2 = qv[2], q3 = qv[3], q4 = qv[4], q5 = qv[5];
+      const Cell o = finish_cell(mom[0] - (int)q0, mom[1] - (int)q1, mom[2] - (int)q2, mom[3] - (int)q3,
+                                 mom[4] - (int)q4, mom[5] - (int)q5, h ? S0[g].y : S0[g].x, h ? S1[g].y : S1[g].x,
+                                 h ? S2[g].y : S2[g].x, h ? S3[g].y : S3[g].x, ref[g][h], T.n_min[pair], ct, st, L);
+      int pc = c + L.ring_x;
+      if (pc >= L.nx) pc -= L.nx;
+      const int64_t i0 = (int64_t)k0 * L.plane + (int64_t)pr * L.nx + pc;
+      const int64_t i1 = (int64_t)k1 * L.plane + (int64_t)pr * L.nx + pc;
+      float* out = L.out;
+      out[i0] = o.z;
+      out[i1] = o.z;
+      out[chs + i0] = o.pitch;
+      out[chs + i1] = -o.pitch;
+      out[2 * chs + i0] = o.roll;
+      out[2 * chs + i1] = -o.roll;
+      out[3 * chs + i0] = o.rough;
+      out[3 * chs + i1] = o.rough;
+      out[4 * chs + i0] = o.risk;
+      out[4 * chs + i1] = o.risk;
+      L.flags[i0] = (uint8_t)o.flags;
+      L.flags[i1] = (uint8_t)o.flags;
+    }
+  }
+}
+
 __global__ void copy_out_kernel(const Launch L, float* __restrict__ dst, uint8_t* __restrict__ fdst) {
   const int64_t total = (int64_t)L.n_yaw * L.plane;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
@@ -398,6 +661,22 @@ __global__ void copy_out_kernel(const Launch L, float* __restrict__ dst, uint8_t
 
 template <typename E, bool COMP>
 cudaError_t launch_typed(const Tables& T, const Launch& L, cudaStream_t stream) {
+  if (!COMP) {
+    size_t pairs = 0;
+    for (int i = 0; i < L.n_rects; ++i) {
+      const int lg = L.rects[i].log_tpr;
+      const size_t sw2 = (size_t)(kG << lg) + 2 * T.rx + 1, sh = (size_t)(kThreads >> lg) + 2 * T.ry;
+      const size_t s = (sh - 1) * sw2;
+      pairs = s > pairs ? s : pairs;
+    }
+    const size_t smem = kMaxStageRows * sizeof(float) + (2 * pairs + 12 * kThreads) * sizeof(float2);
+    auto kern = assess_kernel_x2<E>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid(L.tile_start[L.n_rects], T.n_pairs);
+    kern<<<grid, kThreads, smem, stream>>>(T, L);
+    return cudaGetLastError();
+  }
   size_t smem = 0;
   for (int i = 0; i < L.n_rects; ++i) {
     const size_t s = (size_t)stage_w(L.rects[i].log_tpr, T.rx) * stage_h(L.rects[i].log_tpr, T.ry);

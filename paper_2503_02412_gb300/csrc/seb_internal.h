@@ -61,6 +61,10 @@ struct Launch {
   int32_t tiles_x[kMaxRects];
   uint32_t* err;
   unsigned long long* counters;  // [0] FP64 eigen-solves, [1] degenerate cells
+  // Optional (NULL = off): CTAs of tiles whose flag is 0 exit at once (one flag per tile of a
+  // single-rectangle launch), and only cells whose mask byte is set ([ny][nx]) are stored.
+  const uint8_t* tile_active;
+  const uint8_t* store_mask;
 };
 
 // Control block at the start of every workspace.
@@ -111,6 +115,9 @@ cudaError_t launch_assess(const Tables& T, const Launch& L, int elev_dtype, int 
                           cudaStream_t stream);
 cudaError_t launch_copy_out(const Launch& L, float* out_dev, uint8_t* flags_dev,
                             cudaStream_t stream);
+void launch_defaults(const seb_params& p, const Tables& T, Launch* L);
+void launch_add_rect(Launch& L, int x0, int y0, int w, int h);
+void launch_add_tiles(Launch& L, int x0, int y0, int w, int h);
 
 void set_error(const char* fmt, ...);
 

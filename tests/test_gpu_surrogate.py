@@ -1,0 +1,213 @@
+"""GPU checks of the learned surrogate: every layer, the loss, the gradients and the Adam
+step against the FP64 reference (oracle/surrogate_ref.py) on the GPU's own BF16 inputs; the
+terrain generator against its formula; fully convolutional inference against the batch path;
+the exact fallback; and a short training run that reports what the network gains."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import surrogate_ref as R
+from synthetic import bumpy_plane, fractal_steps_nan
+
+pytestmark = pytest.mark.gpu
+
+C2 = dict(n_yaw=72, res=0.05, length=0.9, width=0.6)
+
+
+@pytest.fixture(scope="module")
+def mods():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2503_02412_gb300 as seb
+    from paper_2503_02412_gb300 import surrogate
+
+    return seb, surrogate
+
+
+def f64(t):
+    return t.detach().float().cpu().numpy().astype(np.float64)
+
+
+def make(mods, nx=96, batch=4, seed=3):
+    seb, surrogate = mods
+    s = surrogate.Surrogate(seb.SebParams(nx=nx, ny=nx, **C2), max_batch=batch)
+    s.init(seed)
+    return s
+
+
+def params_bf16(s):
+    """Reference parameter vector: conv / head weights as the GPU's BF16 copy, biases FP32."""
+    th = f64(s.master)
+    wb = f64(s.weights_bf16)
+    v = s.v
+    for l in range(4):
+        th[v.off_w[l]:v.off_b[l]] = wb[v.off_w[l]:v.off_b[l]]
+    th[v.off_wh:v.off_bh] = wb[v.off_wh:v.off_bh]
+    return th
+
+
+@pytest.mark.parametrize("engine", ["tcgen05", "simt"])
+def test_layers_match_reference(mods, engine):
+    seb, _ = mods
+    s = make(mods)
+    s.set_engine(engine)
+    s.make_batch(np.random.default_rng(0), 4)
+    seb.abi.seb_sur_forward(s.handle, 4)
+    torch.cuda.synchronize()
+    th = params_bf16(s)
+    P = R.unpack(th, s.n_out)
+    x = f64(s.features(4))
+    for l, d in enumerate(R.DILATIONS):
+        ref = np.maximum(R.conv_valid(x, P[2 * l], P[2 * l + 1], d), 0.0)
+        got = f64(s.act(l, 4))
+        err = np.abs(got - ref) - (2 ** -7) * np.abs(ref)
+        assert err.max() <= 1e-5, (l, err.max())
+        x = got  # next layer from the GPU's own stored input
+    ref = x @ P[8].T + P[9]
+    got = f64(s.pred(4))
+    assert np.abs(got - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max())
+
+
+def test_loss_gradients_and_adam_match_reference(mods):
+    seb, _ = mods
+    s = make(mods, batch=3, seed=5)
+    s.make_batch(np.random.default_rng(1), 3)
+    theta0 = params_bf16(s)
+    master0 = f64(s.master)
+    lr = 1e-3
+    s.train_step(3, lr)
+    torch.cuda.synchronize()
+    acts = [f64(s.features(3))] + [f64(s.act(l, 3)) for l in range(4)]
+    pred = f64(s.pred(3))
+    labels = f64(s.labels(3))
+    loss, g, _ = R.loss_and_grad(theta0, acts[0], labels, s.n_out, acts=acts, pred=pred)
+    assert abs(float(s.loss.item()) - loss) <= 1e-5 * max(1.0, loss)
+    gg = f64(s.grad)
+    v = s.v
+    groups = [(v.off_w[l], v.off_b[l]) for l in range(4)] + [(v.off_b[l], v.off_b[l] + 32) for l in range(4)]
+    groups += [(v.off_wh, v.off_bh), (v.off_bh, v.n_params)]
+    for a, b in groups:
+        scale = np.abs(g[a:b]).max() + 1e-30
+        assert np.abs(gg[a:b] - g[a:b]).max() <= 2e-3 * scale, (a, b, np.abs(gg[a:b] - g[a:b]).max(), scale)
+    t1, _, _ = R.adam(master0, gg, np.zeros_like(gg), np.zeros_like(gg), 1, lr)
+    assert np.abs(f64(s.master) - t1).max() <= 1e-6
+
+
+def test_terrain_generator_formula(mods):
+    seb, surrogate = mods
+    rng = np.random.default_rng(2)
+    prm = surrogate.terrain_params(rng, 2, 5.0, noise=0.0)
+    out = torch.empty(2, 100, 100, device="cuda")
+    seb.abi.seb_terrain_bumpy(torch.from_numpy(prm).cuda().data_ptr(), 2, 100, 100, 0.05, 7, out.data_ptr())
+    torch.cuda.synchronize()
+    x = (np.arange(100) + 0.5) * 0.05
+    X, Y = np.meshgrid(x, x)
+    for w in range(2):
+        p = prm[w].astype(np.float64)
+        z = p[0] * (np.cos(p[1]) * X + np.sin(p[1]) * Y)
+        for j in range(8):
+            a, sg, cx, cy = p[4 + 4 * j:8 + 4 * j]
+            z += a * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2 * sg * sg))
+        assert np.abs(out[w].cpu().numpy() - z).max() < 1e-4
+    prm[:, 2] = 0.01
+    seb.abi.seb_terrain_bumpy(torch.from_numpy(prm).cuda().data_ptr(), 2, 100, 100, 0.05, 7, out.data_ptr())
+    prm[:, 2] = 0.0
+    out0 = torch.empty_like(out)
+    seb.abi.seb_terrain_bumpy(torch.from_numpy(prm).cuda().data_ptr(), 2, 100, 100, 0.05, 7, out0.data_ptr())
+    noise = (out - out0).cpu().numpy().ravel()
+    assert abs(noise.std() - 0.01) < 5e-4 and abs(noise.mean()) < 5e-4
+
+
+@pytest.mark.parametrize("engine", ["tcgen05", "simt"])
+def test_map_inference_equals_batch_path(mods, engine):
+    seb, _ = mods
+    s = make(mods, nx=96, batch=1, seed=7)
+    s.set_engine(engine)
+    e = torch.from_numpy(bumpy_plane(8, 96, 96, 0.05)).cuda()
+    out, fl, mask = s.infer(e, exact_fallback=False)
+    exact = torch.zeros(5, 72, 96, 96, device="cuda")
+    centres = torch.tensor([[48, 40]], dtype=torch.int32, device="cuda")
+    seb.abi.seb_sur_gather(s.handle, e.data_ptr(), exact.data_ptr(), 96, 96, centres.data_ptr(), 1, 0)
+    seb.abi.seb_sur_forward(s.handle, 1)
+    torch.cuda.synchronize()
+    pred = s.pred(1)[0].cpu()  # [16][16][144]
+    o = out.cpu()
+    # output cell (i, j) <-> map cell (row 40 - 8 + i, column 48 - 8 + j)
+    for k in (0, 17, 35):
+        assert torch.equal(pred[:, :, 4 * k + 1], o[1, k, 32:48, 40:56])
+        assert torch.equal(pred[:, :, 4 * k + 2], o[2, k, 32:48, 40:56])
+        assert torch.equal(-pred[:, :, 4 * k + 1], o[1, k + 36, 32:48, 40:56])
+    assert ((fl[:, 16:80, 16:80] & seb.abi.SEB_FLAG_SURROGATE) != 0).all()
+
+
+def test_exact_fallback_cells(mods):
+    seb, _ = mods
+    s = make(mods, nx=160, batch=1, seed=9)
+    from synthetic import tilted_plane
+
+    e = tilted_plane(160, 160, 0.05, 0.1, -0.05, 0.0).astype(np.float32)
+    e[70:76, 90:95] = np.nan
+    e[:, 40:] += 0.2  # a step edge between columns 39 and 40
+    te = torch.from_numpy(e).cuda()
+    out, fl, mask = s.infer(te, step=0.04, radius=3, exact_fallback=True)
+    m = seb.SebMap(seb.SebParams(nx=160, ny=160, **C2))
+    m.update(te)
+    ex, exf = m.outputs()
+    mk = mask.cpu().numpy().astype(bool)
+    assert mk[:16].all() and mk[-16:].all() and mk[:, :16].all() and mk[:, -16:].all()
+    assert mk[67:79, 87:98].all()  # radius 3 around the unknown block
+    assert mk[20:140, 36:43].all() and not mk[20:60, 43:50].any()  # radius 3 around the step
+    assert not mk[20:60, 60:80].any()
+    fo, ff, eo, ef = out.cpu(), fl.cpu(), ex.cpu(), exf.cpu()
+    sel = torch.from_numpy(mk)
+    assert torch.equal(fo[:, :, sel].view(torch.int32), eo[:, :, sel].view(torch.int32))
+    assert torch.equal(ff[:, sel], ef[:, sel])
+    assert ((ff[:, ~sel] & seb.abi.SEB_FLAG_SURROGATE) != 0).all()
+
+
+def test_training_gain_report(mods, record_property):
+    """Trains on bumpy-plane patches labelled by the exact kernel, then compares the network
+    with the exact kernel on held-out maps: error on the cells it predicts, fallback share,
+    and time of a full exact rebuild vs surrogate inference with the exact fallback."""
+    seb, surrogate = mods
+    s = surrogate.Surrogate(seb.SebParams(nx=400, ny=400, **C2), max_batch=256)
+    s.init(11)
+    losses = s.train(256 * 160, batch=256, lr=3e-3, seed=4000, log_every=20)
+    record_property("losses", losses)
+    assert losses[-1][1] < 0.5 * losses[0][1]
+    res = {}
+    for name, e in (("bumpy", bumpy_plane(12, 400, 400, 0.05)), ("fractal", fractal_steps_nan(13))):
+        te = torch.from_numpy(e).cuda()
+        m = seb.SebMap(seb.SebParams(nx=400, ny=400, **C2))
+        m.update(te)
+        ex, exf = m.outputs()
+        out, fl, mask = s.infer(te)
+        sur = ((fl & seb.abi.SEB_FLAG_SURROGATE) != 0) & ((exf & 5) == 0)
+        for ch, nm in ((1, "pitch"), (2, "roll"), (4, "risk"), (0, "z")):
+            d = (out[ch] - ex[ch]).abs()[sur]
+            res[f"{name}_{nm}_p50"] = float(d.median())
+            res[f"{name}_{nm}_p99"] = float(torch.quantile(d[:1_000_000].float(), 0.99))
+        res[f"{name}_fallback_frac"] = float(mask.float().mean())
+        # timing (CUDA events, L2 warm: same map, back to back)
+        for _ in range(3):
+            m.update(te)
+            s.infer_into(te, out, fl, mask)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record()
+        for _ in range(10):
+            m.update(te)
+        ev[1].record()
+        for _ in range(10):
+            s.infer_into(te, out, fl, mask)
+        ev[2].record()
+        torch.cuda.synchronize()
+        res[f"{name}_exact_ms"] = ev[0].elapsed_time(ev[1]) / 10
+        res[f"{name}_surrogate_ms"] = ev[1].elapsed_time(ev[2]) / 10
+    for k, v in res.items():
+        record_property(k, v)
+    print(res)
+    assert res["bumpy_pitch_p50"] < 0.05 and res["bumpy_roll_p50"] < 0.05
