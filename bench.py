@@ -37,7 +37,7 @@ WORKLOAD = "se2_map_400x400x72_rebuild_plus_50_shifts"
 
 # ncu DRAM traffic of one full-map rebuild launch (dram__bytes_read.sum + dram__bytes_write.sum),
 # valid only for the kernel source it was captured on (hash of the assess kernel's sources).
-NCU_TRAFFIC = {"sources_sha": "76ccfd40278794e3", "bytes": 22289664 + 206337280}
+NCU_TRAFFIC = {"sources_sha": "8433f9d5e817c422", "bytes": 39397376 + 222850048}
 
 
 def kernel_sources_sha():
@@ -301,7 +301,7 @@ def main():
         "rebuild_ms": rb, "rebuild_cells_per_s": NX * NY * K / (rb * 1e-3),
         "shift_us_mean": (ms_per_step - rb) / N_SHIFTS * 1e3,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "assess_kernel<float,false> (rebuild)",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "assess_kernel_sl<float> (rebuild)",
                      "flop_per_launch": flop, "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x 2070 MHz"},
         "gpu_launches": launches, "fp64_solves": n64, "degenerate": ndeg, "clocks": clk,
     }

@@ -156,9 +156,10 @@ int seb_map_update(seb_map* m, const void* elev_dev, int64_t origin_i, int64_t o
  * whole new window in logical order.  The ring offsets advance by the move, and only the
  * cells whose footprint can see a cell that entered or left the window are recomputed:
  * a band of |move| + reach cells on the entering side and of reach cells on the leaving
- * side, per axis (reach = largest |offset| of any footprint along that axis).  Every
- * other cell keeps its stored value, which is bit-identical to a full rebuild.  A move of
- * at least the window size in either axis falls back to a full rebuild.
+ * side, per axis (reach = largest |offset| of any footprint along that axis, plus 3 columns
+ * / 1 row: cells are computed in 4 x 2 blocks that share a reference height).  Every other
+ * cell keeps its stored value, which is bit-identical to a full rebuild.  A move of at
+ * least the window size in either axis falls back to a full rebuild.
  */
 int seb_map_shift(seb_map* m, const void* elev_dev, int64_t origin_i, int64_t origin_j);
 

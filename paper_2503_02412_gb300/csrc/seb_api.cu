@@ -85,34 +85,19 @@ static Launch base_launch(const seb_map* m, const void* elev) {
   return L;
 }
 
-void push_rect(Launch& L, int x0, int y0, int w, int h, int lg) {
-  if (w <= 0 || h <= 0) return;
-  const int i = L.n_rects++;
-  L.rects[i] = Rect{x0, y0, w, h, lg};
-  const int tw = kG << lg, th = kThreads >> lg;
-  L.tiles_x[i] = (w + tw - 1) / tw;
-  L.tile_start[i + 1] = L.tile_start[i] + L.tiles_x[i] * ((h + th - 1) / th);
+void launch_request(Launch& L, int x0, int y0, int w, int h) {
+  if (w <= 0 || h <= 0 || L.n_req >= 4) return;
+  L.req[L.n_req++] = Rect{x0, y0, w, h, x0, y0, 0};
 }
 
-// A rectangle of cells to recompute, split so that no tile is mostly empty: whole 32 x 32
-// tiles, a right remainder in 8-wide tiles and a bottom remainder in 8-tall tiles.
-void launch_add_rect(Launch& L, int x0, int y0, int w, int h) {
-  if (w <= 0 || h <= 0) return;
-  const int wm = w >= 32 ? w - w % 32 : 0, hm = h >= 32 ? h - h % 32 : 0;
-  if (wm && hm) {
-    push_rect(L, x0, y0, wm, hm, 3);
-    push_rect(L, x0 + wm, y0, w - wm, h, 1);
-    push_rect(L, x0, y0 + hm, wm, h - hm, 5);
-  } else if (w < h) {
-    push_rect(L, x0, y0, w, h, 1);
-  } else {
-    push_rect(L, x0, y0, w, h, 5);
-  }
+void launch_set_origin(Launch& L, int64_t oi, int64_t oj) {
+  L.phase_x = (int32_t)(((oi % 4) + 4) % 4);
+  L.phase_y = (int32_t)(((oj % 2) + 2) % 2);
 }
 
 static int64_t rect_cells(const Launch& L, int n_yaw) {
   int64_t c = 0;
-  for (int i = 0; i < L.n_rects; ++i) c += (int64_t)L.rects[i].w * L.rects[i].h;
+  for (int i = 0; i < L.n_req; ++i) c += (int64_t)L.req[i].w * L.req[i].h;
   return c * n_yaw;
 }
 
@@ -128,10 +113,6 @@ static int check_elev(seb_map* m, const void* elev) {
     return fail(m, SEB_ERR_INVALID_ARG, "elevation must be device memory");
   return SEB_OK;
 }
-
-// One rectangle in whole 32 x 32 tiles (the last row/column ragged), so that tile t of the
-// launch is tile (t % tiles_x, t / tiles_x) of the rectangle's 32 x 32 grid.
-void launch_add_tiles(Launch& L, int x0, int y0, int w, int h) { push_rect(L, x0, y0, w, h, 3); }
 
 }  // namespace seb
 
@@ -228,7 +209,8 @@ int seb_map_update(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
   if (rc) return rc;
   m->ring_x = m->ring_y = 0;
   Launch L = base_launch(m, elev);
-  launch_add_rect(L, 0, 0, m->p.nx, m->p.ny);
+  launch_set_origin(L, oi, oj);
+  launch_request(L, 0, 0, m->p.nx, m->p.ny);
   cudaError_t e = launch_assess(m->T, L, m->p.elev_dtype, m->p.precision, m->stream);
   if (e != cudaSuccess) return cuda_fail(m, e, "assess launch");
   m->last_cells = rect_cells(L, m->p.n_yaw);
@@ -254,7 +236,9 @@ int seb_map_shift(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
   // keeps every surviving cell at its physical address.
   m->ring_x = (int32_t)(((m->ring_x + dx) % nx + nx) % nx);
   m->ring_y = (int32_t)(((m->ring_y + dy) % ny + ny) % ny);
-  const int rx = m->T.rx, ry = m->T.ry;
+  // Bands reach the footprint's extent plus one cell block (cells of a 4 x 2 block share a
+  // reference height, so a block that straddles an edge is recomputed whole).
+  const int rx = m->T.rx + 3, ry = m->T.ry + 1;
   // Column bands: cells that now see entering columns, and cells that used to see columns
   // that left the window.
   int left = 0, right = 0, top = 0, bottom = 0;
@@ -273,13 +257,14 @@ int seb_map_shift(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
     bottom = ry;
   }
   Launch L = base_launch(m, elev);
+  launch_set_origin(L, oi, oj);
   if (left + right >= nx || top + bottom >= ny) {
-    launch_add_rect(L, 0, 0, nx, ny);
+    launch_request(L, 0, 0, nx, ny);
   } else {
-    launch_add_rect(L, 0, 0, left, ny);
-    launch_add_rect(L, nx - right, 0, right, ny);
-    launch_add_rect(L, left, 0, nx - left - right, top);
-    launch_add_rect(L, left, ny - bottom, nx - left - right, bottom);
+    launch_request(L, 0, 0, left, ny);
+    launch_request(L, nx - right, 0, right, ny);
+    launch_request(L, left, 0, nx - left - right, top);
+    launch_request(L, left, ny - bottom, nx - left - right, bottom);
   }
   cudaError_t e = launch_assess(m->T, L, m->p.elev_dtype, m->p.precision, m->stream);
   if (e != cudaSuccess) return cuda_fail(m, e, "assess launch (shift)");

@@ -291,8 +291,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int lg = R.log_tpr;
   const int tw = kG << lg, th = kThreads >> lg;
   const int t = b - L.tile_start[ri];
-  const int tx0 = R.x0 + (t % L.tiles_x[ri]) * tw;
-  const int ty0 = R.y0 + (t / L.tiles_x[ri]) * th;
+  const int tx0 = R.tx + (t % L.tiles_x[ri]) * tw;
+  const int ty0 = R.ty + (t / L.tiles_x[ri]) * th;
   const int rx = T.rx, ry = T.ry;
   const int sw = stage_w(lg, rx), sh = stage_h(lg, ry);
 
@@ -382,220 +382,211 @@ __global__ void __launch_bounds__(kThreads, 2)
 }
 
 // ------------------------------------------------------------------------------------------------
-// Plain-precision kernel on packed FP32 pairs.  Each thread owns a 2 x 2 block of cells; the
-// staged tile is stored as vertical pairs (T[r][c], T[r+1][c]) so that one 8-byte shared load
-// feeds both rows of a column, and the moment updates run as FP32x2 instructions
-// (__fadd2_rn / __ffma2_rn round each half exactly like the scalar forms).  Every cell performs
-// the same operations in the same order as assess_kernel, so the results are bit-identical.
-// Alternate pair rows are skewed by one element, which keeps a half-warp (8 column pairs x 2
-// pair rows) on 32 distinct banks.
+// Plain-precision kernel with sliding row sums on packed FP32 pairs.
+//
+// Cells are grouped in blocks of 4 columns x 2 rows aligned to the global grid (global column
+// = 0 mod 4, global row = 0 mod 2), one block per thread, so that the grouping of a cell never
+// depends on the tile or on the window origin.  The two rows of a block are processed as FP32x2
+// pairs (__fadd2_rn / __ffma2_rn, each half rounded like the scalar forms) from a staged tile
+// of vertical pairs (T[r][c], T[r+1][c]).  All cells of a block are centred on one reference
+// height (the block's first known cell, else the first known footprint cell in run order).
+// For each row run (dj, lo, hi) only the first column of the block is summed point by point,
+// A = sum z', Bx = sum p z', C = sum z'^2 (p = column offset from the block's first column);
+// the next columns follow by sliding the run one cell:
+//   A_g = A_{g-1} - z'(lo+g-1) + z'(hi+g), Bx_g = Bx_{g-1} - (lo+g-1) z'(lo+g-1) + (hi+g) z'(hi+g),
+//   C_g = C_{g-1} - z'(lo+g-1)^2 + z'(hi+g)^2, and sum di z' = Bx_g - g A_g for column g.
+// Runs whose rows (over the warp) hold an unknown cell use weights m (z' = fma(-ref, m, z)) and
+// slide the moments of the missing points the same way; both paths give bit-identical sums
+// for runs without unknown cells.  Alternate pair rows are skewed so that a half-warp (4 blocks
+// x 4 pair rows) reads 32 distinct banks.
+// Layouts (log2 of blocks per row): 3 -> 32 x 64 cells, 2 -> 16 x 128, 5 -> 128 x 16.
 // ------------------------------------------------------------------------------------------------
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return f2(-a.x, -a.y); }
 
-__device__ __forceinline__ int pair_index(int r, int c, int sw2) { return r * sw2 + c + ((r >> 1) & 1); }
+__host__ __device__ inline int sl_tw(int lay) { return 4 << lay; }
+__host__ __device__ inline int sl_th(int lay) { return 2 * (kThreads >> lay); }
+__host__ __device__ inline int sl_sw2(int lay, int rx) { return (sl_tw(lay) + 2 * rx + 3 + 7) & ~7; }
+__device__ __forceinline__ int sl_index(int r, int c, int sw2) { return r * sw2 + c + ((r >> 1) & 3); }
+constexpr int kSlQ = 6 * 4;  // missing-point moments per thread: [k][g] float2 (rows packed)
 
-#ifndef SEB_ASSESS_MIN_BLOCKS
-#define SEB_ASSESS_MIN_BLOCKS 2  // CTAs per SM the register budget is sized for
-#endif
 template <typename E>
-__global__ void __launch_bounds__(kThreads, SEB_ASSESS_MIN_BLOCKS)
-    assess_kernel_x2(const __grid_constant__ Tables T, const __grid_constant__ Launch L) {
+__global__ void __launch_bounds__(kThreads, 2)
+    assess_kernel_sl(const __grid_constant__ Tables T, const __grid_constant__ Launch L) {
   extern __shared__ float smem[];
   int* rowflag = reinterpret_cast<int*>(smem);
-  float2* pt = reinterpret_cast<float2*>(smem + kMaxStageRows);  // [sh - 1][sw2] vertical pairs of heights
-  // (unknown -> 0), then the matching pairs of known weights, then per-thread missing moments
-  float2* pm = pt + (size_t)(kThreads >> 1) * 0;  // placeholder, set below once sh, sw2 are known
+  float2* qs = reinterpret_cast<float2*>(smem + kMaxStageRows);  // [kSlQ][kThreads]
+  float2* pt = qs + kSlQ * kThreads;                             // [sh - 1][sw2] vertical pairs
   if (blockDim.x != kThreads || blockIdx.y >= (unsigned)T.n_pairs) {
     if (threadIdx.x == 0) atomicOr(L.err, kErrLaunchShape);
     return;
   }
   const int b = blockIdx.x;
-  if (L.tile_active && !L.tile_active[b]) return;  // uniform per CTA, before any barrier
   int ri = 0;
 #pragma unroll 1
   while (ri + 1 < L.n_rects && b >= L.tile_start[ri + 1]) ++ri;
   const Rect R = L.rects[ri];
-  const int lg = R.log_tpr;
-  const int tw = kG << lg, th = kThreads >> lg;
+  const int lay = R.log_tpr;
+  const int tw = sl_tw(lay), th = sl_th(lay);
   const int t = b - L.tile_start[ri];
-  const int tx0 = R.x0 + (t % L.tiles_x[ri]) * tw;
-  const int ty0 = R.y0 + (t / L.tiles_x[ri]) * th;
+  const int tx0 = R.tx + (t % L.tiles_x[ri]) * tw;
+  const int ty0 = R.ty + (t / L.tiles_x[ri]) * th;
   const int rx = T.rx, ry = T.ry;
-  const int sw = tw + 2 * rx, sh = th + 2 * ry;
-  const int sw2 = sw + 1;
+  const int sw = tw + 2 * rx, sh = th + 2 * ry, sw2 = sl_sw2(lay, rx);
+  const int tid = threadIdx.x;
 
-  const int npair = (sh - 1) * sw2;
-  pm = pt + npair;
-  float2* qs = pm + npair;  // [6][kThreads] float2 per column of the thread: [g][k][tid]
-  for (int i = threadIdx.x; i < sh; i += kThreads) rowflag[i] = 0;
-  for (int i = threadIdx.x; i < 12 * kThreads; i += kThreads) qs[i] = make_float2(0.f, 0.f);
+  for (int i = tid; i < sh; i += kThreads) rowflag[i] = 0;
+  for (int i = tid; i < kSlQ * kThreads; i += kThreads) qs[i] = make_float2(0.f, 0.f);
   __syncthreads();
   const E* __restrict__ elev = static_cast<const E*>(L.elev);
-  for (int idx = threadIdx.x; idx < sw * sh; idx += kThreads) {
+  const float qnan = __int_as_float(0x7fc00000);
+  for (int idx = tid; idx < sw * sh; idx += kThreads) {
     const int row = idx / sw, col = idx - row * sw;
     const int gy = ty0 - ry + row, gx = tx0 - rx + col;
-    float v = 0.f, m = 0.f;
-    if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) {
-      const float e = to_f32<E>(elev[(int64_t)gy * L.nx + gx]);
-      if (e == e) {
-        v = e;
-        m = 1.f;
-      }
-    }
-    if (m == 0.f) rowflag[row] = 1;
-    if (row < sh - 1) {
-      const int k = pair_index(row, col, sw2);
-      pt[k].x = v;
-      pm[k].x = m;
-    }
-    if (row > 0) {
-      const int k = pair_index(row - 1, col, sw2);
-      pt[k].y = v;
-      pm[k].y = m;
-    }
+    float v = qnan;
+    if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) v = to_f32<E>(elev[(int64_t)gy * L.nx + gx]);
+    if (v != v) rowflag[row] = 1;
+    if (row < sh - 1) pt[sl_index(row, col, sw2)].x = v;
+    if (row > 0) pt[sl_index(row - 1, col, sw2)].y = v;
   }
   __syncthreads();
 
-  // 2 x 2 cells per thread: column pair cp, row pair rp (see the bank note above).
-  const int cpr = (tw >> 1);                   // column pairs per row
-  const int g8 = cpr < 8 ? cpr : 8;
-  const int tid = threadIdx.x;
-  const int cp = (tid % g8) + g8 * ((tid / (2 * g8)) % (cpr / g8));
-  const int rp = ((tid / g8) & 1) + 2 * (tid / (2 * cpr));
-  const int lx = 2 * cp, ly = 2 * rp;
+  // block (cb, rp) of this thread: a half-warp holds 4 blocks x 4 pair rows
+  const int cbs = 1 << lay, c4 = cbs >> 2;
+  const int cb = (tid & 3) + 4 * ((tid >> 4) % c4);
+  const int rp = ((tid >> 2) & 3) + 4 * ((tid >> 4) / c4);
+  const int lx = 4 * cb, ly = 2 * rp;
   const int cx = tx0 + lx, cy = ty0 + ly;
+  auto stores = [&](int c, int r) { return c >= R.x0 && c < R.x0 + R.w && r >= R.y0 && r < R.y0 + R.h; };
   if (L.store_mask) {
-    // masked-store launch: a warp without a cell to store skips the work (warp-uniform,
-    // after the last barrier)
+    // masked-store launch: a warp without a cell to store skips the work (warp-uniform)
     int need = 0;
     for (int h = 0; h < 2; ++h)
-      for (int g = 0; g < 2; ++g) {
-        const int c = cx + g, r = cy + h;
-        if (c < R.x0 + R.w && r < R.y0 + R.h && L.store_mask[(int64_t)r * L.nx + c]) need = 1;
-      }
+      for (int g = 0; g < 4; ++g)
+        if (stores(cx + g, cy + h) && L.store_mask[(int64_t)(cy + h) * L.nx + cx + g]) need = 1;
     if (!__any_sync(0xffffffffu, need)) return;
   }
   const int pair = blockIdx.y;
   const int r0 = T.run_start[pair], r1 = T.run_start[pair + 1];
-  const float qnan = __int_as_float(0x7fc00000);
-  auto tile_at = [&](int row, int col) {  // staged height (row, col), NaN when unknown
-    const int k = row < sh - 1 ? pair_index(row, col, sw2) : pair_index(row - 1, col, sw2);
-    const float v = row < sh - 1 ? pt[k].x : pt[k].y, m = row < sh - 1 ? pm[k].x : pm[k].y;
-    return m != 0.f ? v : qnan;
+  auto tile_at = [&](int row, int col) {
+    return row < sh - 1 ? pt[sl_index(row, col, sw2)].x : pt[sl_index(row - 1, col, sw2)].y;
   };
-
-  // references: the centre height, else the first known footprint cell in run order
-  float ref[2][2];  // [col g][row h]
-#pragma unroll
-  for (int g = 0; g < 2; ++g)
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      float r = tile_at(ry + ly + h, rx + lx + g);
-      if (r != r) {
-        r = 0.f;
-        bool found = false;
-        for (int q = r0; q < r1 && !found; ++q) {
-          const uint32_t pk = T.runs[q];
-          const int dj = unpack(pk, 0), lo = unpack(pk, 8), hi = unpack(pk, 16);
-          for (int d = lo; d <= hi; ++d) {
-            const float v = tile_at(ry + ly + h + dj, rx + lx + g + d);
-            if (v == v) {
-              r = v;
-              found = true;
-              break;
-            }
-          }
-        }
-      }
-      ref[g][h] = r;
+  // block reference: first known cell of the block (rows outer), else of the footprint of
+  // its first cell in run order, else 0 (then every cell of the block is unknown)
+  float ref = qnan;
+  for (int h = 0; h < 2 && ref != ref; ++h)
+    for (int g = 0; g < 4 && ref != ref; ++g) ref = tile_at(ry + ly + h, rx + lx + g);
+  if (ref != ref) {
+    for (int q = r0; q < r1 && ref != ref; ++q) {
+      const uint32_t pk = T.runs[q];
+      const int dj = unpack(pk, 0), lo = unpack(pk, 8), hi = unpack(pk, 16);
+      for (int d = lo; d <= hi && ref != ref; ++d) ref = tile_at(ry + ly + dj, rx + lx + d);
     }
-  const float2 nref[2] = {f2(-ref[0][0], -ref[0][1]), f2(-ref[1][0], -ref[1][1])};
-  const float2 mref[2] = {nref[0], nref[1]};
+    if (ref != ref) ref = 0.f;
+  }
+  const float2 nref = f2(-ref, -ref), one2 = f2(1.f, 1.f), zero2 = f2(0.f, 0.f);
 
-  float2 S0[2], S1[2], S2[2], S3[2];
+  float2 S0[4], S1[4], S2[4], S3[4];
 #pragma unroll
-  for (int g = 0; g < 2; ++g) S0[g] = S1[g] = S2[g] = S3[g] = f2(0.f, 0.f);
-  const int tq = threadIdx.x;
-  auto Qs = [&](int k, int g) -> float2& { return qs[(g * 6 + k) * kThreads + tq]; };
-  const float2 one2 = f2(1.f, 1.f);
+  for (int g = 0; g < 4; ++g) S0[g] = S1[g] = S2[g] = S3[g] = zero2;
+  auto Qs = [&](int k, int g) -> float2& { return qs[(k * 4 + g) * kThreads + tid]; };
+
   for (int q = r0; q < r1; ++q) {
     const uint32_t pk = T.runs[q];
     const int dj = unpack(pk, 0), lo = unpack(pk, 8), hi = unpack(pk, 16);
-    const int row = ry + ly + dj;  // pair row of this thread for the run
+    const int row = ry + ly + dj;
     const bool masked = __any_sync(0xffffffffu, rowflag[row] | rowflag[row + 1]);
-    const int base = pair_index(row, rx + lx + lo, sw2);
-    const float2* pq = pt + base;
-    const float2* pw = pm + base;
+    const float2* pq = pt + sl_index(row, rx + lx + lo, sw2);  // pq[k]: column lo + k of the block
     const int len = hi - lo + 1;
-    float2 a[2], bb[2], s3[2];
-#pragma unroll
-    for (int g = 0; g < 2; ++g) a[g] = bb[g] = s3[g] = f2(0.f, 0.f);
-    float2 di2 = f2((float)lo, (float)lo);
+    const float flo = (float)lo, fhi = (float)hi;
+    float2 A[4], B[4], C[4];
     if (!masked) {
-      float2 w0 = pq[0];
+      float2 Ab = zero2, Bx = zero2, Cb = zero2, pf = f2(flo, flo);
 #pragma unroll 4
-      for (int i = 0; i < len; ++i) {
-        const float2 w1 = pq[i + 1];
-        float2 zp = add2(w0, nref[0]);
-        a[0] = add2(a[0], zp);
-        bb[0] = fma2(di2, zp, bb[0]);
-        s3[0] = fma2(zp, zp, s3[0]);
-        zp = add2(w1, nref[1]);
-        a[1] = add2(a[1], zp);
-        bb[1] = fma2(di2, zp, bb[1]);
-        s3[1] = fma2(zp, zp, s3[1]);
-        w0 = w1;
-        di2 = add2(di2, one2);
+      for (int k = 0; k < len; ++k) {
+        const float2 zp = add2(pq[k], nref);
+        Ab = add2(Ab, zp);
+        Bx = fma2(pf, zp, Bx);
+        Cb = fma2(zp, zp, Cb);
+        pf = add2(pf, one2);
+      }
+      A[0] = Ab;
+      B[0] = Bx;
+      C[0] = Cb;
+#pragma unroll
+      for (int g = 1; g < 4; ++g) {
+        const float2 zo = add2(pq[g - 1], nref), zi = add2(pq[len - 1 + g], nref);
+        const float po = flo + (float)(g - 1), pi = fhi + (float)g;
+        A[g] = add2(add2(A[g - 1], neg2(zo)), zi);
+        Bx = fma2(f2(pi, pi), zi, fma2(f2(-po, -po), zo, Bx));
+        C[g] = fma2(zi, zi, fma2(neg2(zo), zo, C[g - 1]));
+        B[g] = fma2(f2(-(float)g, -(float)g), A[g], Bx);
       }
     } else {
-      // unknown heights were staged as 0 with weight 0: z' = fma(-ref, m, z) is exactly
-      // z - ref for known points and 0 for unknown ones; x = 1 - m counts the missing points
-      float2 z0 = pq[0], m0 = pw[0];
-      float2 qn[2], qx[2], qxx[2];
-#pragma unroll
-      for (int g = 0; g < 2; ++g) qn[g] = qx[g] = qxx[g] = f2(0.f, 0.f);
-      const float2 neg1 = f2(-1.f, -1.f);
+      // unknown heights: weight m = 0, z' = fma(-ref, m, z) = 0; x = 1 - m counts them
+      auto zof = [&](int k, float2& zp, float2& x) {
+        const float2 v = pq[k];
+        const bool kx = v.x == v.x, ky = v.y == v.y;
+        const float2 m = f2(kx ? 1.f : 0.f, ky ? 1.f : 0.f);
+        zp = fma2(nref, m, f2(kx ? v.x : 0.f, ky ? v.y : 0.f));
+        x = f2(kx ? 0.f : 1.f, ky ? 0.f : 1.f);
+      };
+      float2 Ab = zero2, Bx = zero2, Cb = zero2, pf = f2(flo, flo);
+      float2 qn = zero2, qx = zero2, qxx = zero2;
 #pragma unroll 2
-      for (int i = 0; i < len; ++i) {
-        const float2 z1 = pq[i + 1], m1 = pw[i + 1];
-        const float2 d2 = __fmul2_rn(di2, di2);
-        const float2 zs[2] = {z0, z1}, ms[2] = {m0, m1};
-#pragma unroll
-        for (int g = 0; g < 2; ++g) {
-          const float2 zp = fma2(mref[g], ms[g], zs[g]);
-          const float2 x = fma2(neg1, ms[g], one2);
-          a[g] = add2(a[g], zp);
-          bb[g] = fma2(di2, zp, bb[g]);
-          s3[g] = fma2(zp, zp, s3[g]);
-          qn[g] = add2(qn[g], x);
-          qx[g] = fma2(di2, x, qx[g]);
-          qxx[g] = fma2(d2, x, qxx[g]);
-        }
-        z0 = z1;
-        m0 = m1;
-        di2 = add2(di2, one2);
+      for (int k = 0; k < len; ++k) {
+        float2 zp, x;
+        zof(k, zp, x);
+        Ab = add2(Ab, zp);
+        Bx = fma2(pf, zp, Bx);
+        Cb = fma2(zp, zp, Cb);
+        qn = add2(qn, x);
+        qx = fma2(pf, x, qx);
+        qxx = fma2(__fmul2_rn(pf, pf), x, qxx);
+        pf = add2(pf, one2);
       }
+      A[0] = Ab;
+      B[0] = Bx;
+      C[0] = Cb;
       const float fdj = (float)dj;
       const float2 dj2 = f2(fdj, fdj), dj22 = f2(fdj * fdj, fdj * fdj);
 #pragma unroll
-      for (int g = 0; g < 2; ++g) {
-        Qs(0, g) = add2(Qs(0, g), qn[g]);
-        Qs(1, g) = add2(Qs(1, g), qx[g]);
-        Qs(2, g) = fma2(dj2, qn[g], Qs(2, g));
-        Qs(3, g) = add2(Qs(3, g), qxx[g]);
-        Qs(4, g) = fma2(dj2, qx[g], Qs(4, g));
-        Qs(5, g) = fma2(dj22, qn[g], Qs(5, g));
+      for (int g = 0; g < 4; ++g) {
+        if (g > 0) {
+          float2 zo, xo, zi, xi;
+          zof(g - 1, zo, xo);
+          zof(len - 1 + g, zi, xi);
+          const float po = flo + (float)(g - 1), pi = fhi + (float)g;
+          const float2 po2 = f2(po, po), pi2 = f2(pi, pi);
+          A[g] = add2(add2(A[g - 1], neg2(zo)), zi);
+          Bx = fma2(pi2, zi, fma2(neg2(po2), zo, Bx));
+          C[g] = fma2(zi, zi, fma2(neg2(zo), zo, C[g - 1]));
+          B[g] = fma2(f2(-(float)g, -(float)g), A[g], Bx);
+          qn = add2(add2(qn, neg2(xo)), xi);
+          qx = fma2(pi2, xi, fma2(neg2(po2), xo, qx));
+          qxx = fma2(__fmul2_rn(pi2, pi2), xi, fma2(neg2(__fmul2_rn(po2, po2)), xo, qxx));
+        }
+        // missing-point moments of column g in its own offsets di = p - g
+        const float fg = (float)g;
+        const float2 sdi = fma2(f2(-fg, -fg), qn, qx);
+        const float2 sdi2 = fma2(f2(fg * fg, fg * fg), qn, fma2(f2(-2.f * fg, -2.f * fg), qx, qxx));
+        Qs(0, g) = add2(Qs(0, g), qn);
+        Qs(1, g) = add2(Qs(1, g), sdi);
+        Qs(2, g) = fma2(dj2, qn, Qs(2, g));
+        Qs(3, g) = add2(Qs(3, g), sdi2);
+        Qs(4, g) = fma2(dj2, sdi, Qs(4, g));
+        Qs(5, g) = fma2(dj22, qn, Qs(5, g));
       }
     }
     const float2 dj2 = f2((float)dj, (float)dj);
 #pragma unroll
-    for (int g = 0; g < 2; ++g) {
-      S0[g] = add2(S0[g], a[g]);
-      S1[g] = add2(S1[g], bb[g]);
-      S2[g] = fma2(dj2, a[g], S2[g]);
-      S3[g] = add2(S3[g], s3[g]);
+    for (int g = 0; g < 4; ++g) {
+      S0[g] = add2(S0[g], A[g]);
+      S1[g] = add2(S1[g], B[g]);
+      S2[g] = fma2(dj2, A[g], S2[g]);
+      S3[g] = add2(S3[g], C[g]);
     }
   }
 
@@ -605,22 +596,21 @@ __global__ void __launch_bounds__(kThreads, SEB_ASSESS_MIN_BLOCKS)
   const int* mom = T.mom[pair];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    const int cyh = cy + h;
-    if (cyh >= R.y0 + R.h) break;
-    int pr = cyh + L.ring_y;
+    const int r = cy + h;
+    int pr = r + L.ring_y;
     if (pr >= L.ny) pr -= L.ny;
 #pragma unroll
-    for (int g = 0; g < 2; ++g) {
+    for (int g = 0; g < 4; ++g) {
       const int c = cx + g;
-      if (c >= R.x0 + R.w) break;
-      if (L.store_mask && !L.store_mask[(int64_t)cyh * L.nx + c]) continue;
+      if (!stores(c, r)) continue;
+      if (L.store_mask && !L.store_mask[(int64_t)r * L.nx + c]) continue;
       float qv[6];
 #pragma unroll
       for (int k = 0; k < 6; ++k) qv[k] = h ? Qs(k, g).y : Qs(k, g).x;
-      const float q0 = qv[0], q1 = qv[1], q2 = qv[2], q3 = qv[3], q4 = qv[4], q5 = qv[5];
-      const Cell o = finish_cell(mom[0] - (int)q0, mom[1] - (int)q1, mom[2] - (int)q2, mom[3] - (int)q3,
-                                 mom[4] - (int)q4, mom[5] - (int)q5, h ? S0[g].y : S0[g].x, h ? S1[g].y : S1[g].x,
-                                 h ? S2[g].y : S2[g].x, h ? S3[g].y : S3[g].x, ref[g][h], T.n_min[pair], ct, st, L);
+      const Cell o = finish_cell(mom[0] - (int)qv[0], mom[1] - (int)qv[1], mom[2] - (int)qv[2], mom[3] - (int)qv[3],
+                                 mom[4] - (int)qv[4], mom[5] - (int)qv[5], h ? S0[g].y : S0[g].x,
+                                 h ? S1[g].y : S1[g].x, h ? S2[g].y : S2[g].x, h ? S3[g].y : S3[g].x, ref,
+                                 T.n_min[pair], ct, st, L);
       int pc = c + L.ring_x;
       if (pc >= L.nx) pc -= L.nx;
       const int64_t i0 = (int64_t)k0 * L.plane + (int64_t)pr * L.nx + pc;
@@ -659,24 +649,96 @@ __global__ void copy_out_kernel(const Launch L, float* __restrict__ dst, uint8_t
   }
 }
 
-template <typename E, bool COMP>
-cudaError_t launch_typed(const Tables& T, const Launch& L, cudaStream_t stream) {
-  if (!COMP) {
-    size_t pairs = 0;
-    for (int i = 0; i < L.n_rects; ++i) {
-      const int lg = L.rects[i].log_tpr;
-      const size_t sw2 = (size_t)(kG << lg) + 2 * T.rx + 1, sh = (size_t)(kThreads >> lg) + 2 * T.ry;
-      const size_t s = (sh - 1) * sw2;
-      pairs = s > pairs ? s : pairs;
+// Tiling of the requested rectangles for assess_kernel (v2 layouts, tiles start at the
+// rectangle's corner).
+void decompose_v2(Launch& L) {
+  L.n_rects = 0;
+  L.tile_start[0] = 0;
+  auto push = [&](int x0, int y0, int w, int h, int lg) {
+    if (w <= 0 || h <= 0) return;
+    const int i = L.n_rects++;
+    L.rects[i] = Rect{x0, y0, w, h, x0, y0, lg};
+    const int tw = kG << lg, th = kThreads >> lg;
+    L.tiles_x[i] = (w + tw - 1) / tw;
+    L.tile_start[i + 1] = L.tile_start[i] + L.tiles_x[i] * ((h + th - 1) / th);
+  };
+  for (int k = 0; k < L.n_req; ++k) {
+    const Rect q = L.req[k];
+    const int wm = q.w >= 32 ? q.w - q.w % 32 : 0, hm = q.h >= 32 ? q.h - q.h % 32 : 0;
+    if (wm && hm) {
+      push(q.x0, q.y0, wm, hm, 3);
+      push(q.x0 + wm, q.y0, q.w - wm, q.h, 1);
+      push(q.x0, q.y0 + hm, wm, q.h - hm, 5);
+    } else if (q.w < q.h) {
+      push(q.x0, q.y0, q.w, q.h, 1);
+    } else {
+      push(q.x0, q.y0, q.w, q.h, 5);
     }
-    const size_t smem = kMaxStageRows * sizeof(float) + (2 * pairs + 12 * kThreads) * sizeof(float2);
-    auto kern = assess_kernel_x2<E>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const dim3 grid(L.tile_start[L.n_rects], T.n_pairs);
-    kern<<<grid, kThreads, smem, stream>>>(T, L);
-    return cudaGetLastError();
   }
+}
+
+// Tiling for assess_kernel_sl: tile grids start on globally aligned blocks (column = 0 mod 4,
+// row = 0 mod 2 in global cells), so a rectangle's grid may start up to 3 columns / 1 row
+// before it; those cells are computed but not stored.
+void decompose_sl(Launch& L) {
+  L.n_rects = 0;
+  L.tile_start[0] = 0;
+  auto push = [&](int tx, int ty, int sx0, int sy0, int sx1, int sy1, int lay) {
+    if (sx1 <= sx0 || sy1 <= sy0) return;
+    const int i = L.n_rects++;
+    L.rects[i] = Rect{sx0, sy0, sx1 - sx0, sy1 - sy0, tx, ty, lay};
+    const int tw = sl_tw(lay), th = sl_th(lay);
+    L.tiles_x[i] = (sx1 - tx + tw - 1) / tw;
+    L.tile_start[i + 1] = L.tile_start[i] + L.tiles_x[i] * ((sy1 - ty + th - 1) / th);
+  };
+  for (int k = 0; k < L.n_req; ++k) {
+    const Rect q = L.req[k];
+    const int ax = q.x0 - (((q.x0 + L.phase_x) % 4) + 4) % 4;
+    const int ay = q.y0 - (((q.y0 + L.phase_y) % 2) + 2) % 2;
+    const int x1 = q.x0 + q.w, y1 = q.y0 + q.h;
+    const int W = x1 - ax, H = y1 - ay;
+    if (W >= 32 && H >= 64) {
+      const int Wm = W - W % 32, Hm = H - H % 64;
+      push(ax, ay, q.x0, q.y0, ax + Wm, ay + Hm, 3);
+      push(ax + Wm, ay, ax + Wm, q.y0, x1, y1, 2);
+      push(ax, ay + Hm, q.x0, ay + Hm, ax + Wm, y1, 5);
+    } else if (W < H) {
+      push(ax, ay, q.x0, q.y0, x1, y1, 2);
+    } else {
+      push(ax, ay, q.x0, q.y0, x1, y1, 5);
+    }
+  }
+}
+
+size_t smem_sl(const Tables& T, const Launch& L) {
+  size_t pairs = 0;
+  for (int i = 0; i < L.n_rects; ++i) {
+    const int lay = L.rects[i].log_tpr;
+    const size_t s = (size_t)(sl_th(lay) + 2 * T.ry - 1) * sl_sw2(lay, T.rx);
+    pairs = s > pairs ? s : pairs;
+  }
+  return kMaxStageRows * sizeof(float) + ((size_t)kSlQ * kThreads + pairs) * sizeof(float2);
+}
+
+template <typename E, bool COMP>
+cudaError_t launch_typed(const Tables& T, const Launch& Lreq, cudaStream_t stream) {
+  Launch L = Lreq;
+  if (!COMP) {
+    decompose_sl(L);
+    const size_t smem = smem_sl(T, L);
+    if (smem <= 227 * 1024) {
+      if (L.tile_start[L.n_rects] == 0) return cudaSuccess;
+      auto kern = assess_kernel_sl<E>;
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      const dim3 grid(L.tile_start[L.n_rects], T.n_pairs);
+      kern<<<grid, kThreads, smem, stream>>>(T, L);
+      return cudaGetLastError();
+    }
+    // very large footprints: the per-cell kernel below
+  }
+  decompose_v2(L);
+  if (L.tile_start[L.n_rects] == 0) return cudaSuccess;
   size_t smem = 0;
   for (int i = 0; i < L.n_rects; ++i) {
     const size_t s = (size_t)stage_w(L.rects[i].log_tpr, T.rx) * stage_h(L.rects[i].log_tpr, T.ry);
@@ -696,7 +758,7 @@ cudaError_t launch_typed(const Tables& T, const Launch& L, cudaStream_t stream) 
 
 cudaError_t launch_assess(const Tables& T, const Launch& L, int elev_dtype, int precision,
                           cudaStream_t stream) {
-  if (L.tile_start[L.n_rects] == 0) return cudaSuccess;
+  if (L.n_req == 0) return cudaSuccess;
   const bool comp = precision == SEB_COMPENSATED;
   switch (elev_dtype) {
     case SEB_F32:

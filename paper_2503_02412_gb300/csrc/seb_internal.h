@@ -37,8 +37,9 @@ struct Tables {
 };
 
 struct Rect {
-  int32_t x0, y0, w, h;
-  int32_t log_tpr;  // layout: log2 of threads per row
+  int32_t x0, y0, w, h;  // cells stored: [x0, x0 + w) x [y0, y0 + h)
+  int32_t tx, ty;        // origin of the tile grid (<= x0, y0)
+  int32_t log_tpr;       // layout (see the kernels)
 };
 
 // Everything else a launch needs (by value, in the parameter bank).
@@ -55,6 +56,9 @@ struct Launch {
   float w0, w1, w2;
   float gap_fp64;
   int32_t narrow_moments;  // N * sum di^2 etc. fit in int32
+  int32_t n_req;          // rectangles of cells to recompute, before tiling
+  Rect req[4];
+  int32_t phase_x, phase_y;  // window origin mod 4 / mod 2 (global alignment of cell blocks)
   int32_t n_rects;
   Rect rects[kMaxRects];
   int32_t tile_start[kMaxRects + 1];
@@ -116,8 +120,8 @@ cudaError_t launch_assess(const Tables& T, const Launch& L, int elev_dtype, int 
 cudaError_t launch_copy_out(const Launch& L, float* out_dev, uint8_t* flags_dev,
                             cudaStream_t stream);
 void launch_defaults(const seb_params& p, const Tables& T, Launch* L);
-void launch_add_rect(Launch& L, int x0, int y0, int w, int h);
-void launch_add_tiles(Launch& L, int x0, int y0, int w, int h);
+void launch_request(Launch& L, int x0, int y0, int w, int h);
+void launch_set_origin(Launch& L, int64_t origin_i, int64_t origin_j);
 
 void set_error(const char* fmt, ...);
 

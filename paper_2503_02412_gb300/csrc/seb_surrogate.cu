@@ -1073,9 +1073,8 @@ int seb_sur_infer(seb_sur* h, const float* elev, float step, int32_t radius, int
   L.flags = flags;
   L.err = h->err;
   L.counters = reinterpret_cast<unsigned long long*>(h->err + 2);
-  L.tile_active = tiles;
   L.store_mask = mask;
-  seb::launch_add_tiles(L, 0, 0, nx, ny);
+  seb::launch_request(L, 0, 0, nx, ny);
   return cuda_check(seb::launch_assess(h->T, L, h->p.elev_dtype, h->p.precision, st), "exact fallback");
 }
 
