@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rows", action="store_true", help="skip the per-row measurements")
+    ap.add_argument("--sur-patches", type=int, default=200_000, help="surrogate training patches")
     ap.add_argument("--profile-rebuild", action="store_true",
                     help="only run three full rebuilds of the map (a short program for ncu)")
     return ap.parse_args()
@@ -150,6 +152,23 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def max_over_ranks(x, device):
+    """Maximum of a float over the ranks of the job (the job's time is its slowest rank)."""
+    import torch
+    import torch.distributed as dist
+
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(cells_per_rank, world_size, job_ms):
+    """Whole-job throughput: every rank (a replica) assesses its own map."""
+    return cells_per_rank * world_size / (job_ms / 1e3)
 
 
 def flush_l2(buf):
@@ -268,13 +287,11 @@ def main():
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     n64, ndeg = m.check()
+    total_ms = max_over_ranks(total_ms, dev)
     if world_size > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
         torch.distributed.barrier()
     ms_per_step = total_ms / args.steps
-    value = cells_total * world_size / (total_ms / 1e3)
+    value = job_value(cells_total, world_size, total_ms)
 
     # roofline of the dominant kernel (the full-map rebuild launch)
     props = torch.cuda.get_device_properties(dev)
@@ -289,6 +306,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(seb, m, world_np, origins, args, dev)
+    rows = None if args.no_rows or world_size > 1 else measure_rows(seb, args, dev)
     line = {
         "metric": "SE(2) cells/s (400x400x72 map: full rebuild + 50 rolling shifts per step)",
         "value": value, "unit": "SE(2) cells/s", "n_gpus": world_size, "steps": args.steps,
@@ -307,12 +325,107 @@ def main():
     }
     if e2e is not None:
         line["e2e"] = e2e
+    if rows is not None:
+        line["rows"] = rows
     if rank == 0 and world_size == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(world_np, origins, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line))
     if world_size > 1:
         torch.distributed.destroy_process_group()
+
+
+def _time(fn, reps, stream):
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def measure_rows(seb, args, dev):
+    """The other rows of the hot path, each on its own configuration, outside the timed step:
+    continuous-pose query forward / backward (1,048,576 poses on the 100x100 map), the
+    reduced-precision rebuild (1024x1024x72, FP32 / BF16 / FP16 elevation) and the learned
+    surrogate against the exact kernel on the 400x400x72 map."""
+    import torch
+
+    from paper_2503_02412_gb300 import abi
+    from paper_2503_02412_gb300.surrogate import Surrogate
+    from synthetic import bumpy_plane, fractal_steps_nan, random_poses
+
+    st = torch.cuda.current_stream(dev)
+    rows = {}
+    # S9 / S10
+    pq = seb.SebParams(nx=100, ny=100, n_yaw=36, res=0.1, length=0.6, width=0.4)
+    e = torch.from_numpy(bumpy_plane(0)).to(dev)
+    n = 1 << 20
+    poses = torch.from_numpy(random_poses(4, n, 100, 100, 0.1, 5)).to(dev)
+    out = torch.empty(n, 5, device=dev)
+    fl = torch.empty(n, dtype=torch.uint8, device=dev)
+    sv = torch.empty(n, abi.SEB_QUERY_SAVED, device=dev)
+    g = torch.randn(n, 5, device=dev)
+    gp = torch.empty(n, 3, device=dev)
+    c = pq.c()
+    fwd = lambda: abi.seb_query_poses(c, e.data_ptr(), 0, 0, poses.data_ptr(), n, out.data_ptr(), fl.data_ptr(),  # noqa: E731
+                                      sv.data_ptr(), st.cuda_stream)
+    bwd = lambda: abi.seb_query_poses_backward(c, e.data_ptr(), 0, 0, poses.data_ptr(), sv.data_ptr(),  # noqa: E731
+                                               g.data_ptr(), gp.data_ptr(), n, st.cuda_stream)
+    tf, tb = _time(fwd, 10, st), _time(bwd, 10, st)
+    rows["query_1M_poses"] = {"fwd_ms": tf, "bwd_ms": tb, "fwd_poses_per_s": n / tf * 1e3,
+                              "bwd_poses_per_s": n / tb * 1e3, "config": "100x100 map at 0.1 m, 0.6x0.4 m"}
+    del poses, out, fl, sv, g, gp
+    # S8
+    e3 = torch.from_numpy(bumpy_plane(21, 1024, 1024, 0.05)).to(dev)
+    prec = {}
+    for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16), ("f16", torch.float16)):
+        m = seb.SebMap(seb.SebParams(nx=1024, ny=1024, n_yaw=72, res=0.05, length=0.9, width=0.6, elev_dtype=dt), dev)
+        ed = e3.to(dt)
+        t = _time(lambda: m.update(ed), 5, st)
+        prec[name] = {"rebuild_ms": t, "cells_per_s": 1024 * 1024 * 72 / t * 1e3}
+        del m
+        torch.cuda.empty_cache()
+    mc = seb.SebMap(seb.SebParams(nx=1024, ny=1024, n_yaw=72, res=0.05, length=0.9, width=0.6,
+                                  precision="compensated"), dev)
+    t = _time(lambda: mc.update(e3), 5, st)
+    prec["f32_compensated"] = {"rebuild_ms": t, "cells_per_s": 1024 * 1024 * 72 / t * 1e3}
+    del mc
+    torch.cuda.empty_cache()
+    rows["precision_1024x1024x72"] = prec
+    # S11 / S12
+    C2 = dict(nx=NX, ny=NY, n_yaw=K, res=RES, length=LENGTH, width=WIDTH)
+    sur = Surrogate(seb.SebParams(**C2), max_batch=256, device=dev)
+    sur.init(11)
+    t0 = time.perf_counter()
+    losses = sur.train(args.sur_patches, batch=256, lr=3e-3, seed=4000, log_every=50)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    em = torch.from_numpy(fractal_steps_nan(13)).to(dev)
+    m = seb.SebMap(seb.SebParams(**C2), dev)
+    m.update(em)
+    ex, exf = m.outputs()
+    o, f, mk = sur.infer(em)
+    surc = ((f & abi.SEB_FLAG_SURROGATE) != 0) & ((exf & 5) == 0)
+    err = {}
+    for ch, nm in ((0, "z"), (1, "pitch"), (2, "roll"), (4, "risk")):
+        d = (o[ch] - ex[ch]).abs()[surc]
+        err[nm + "_p50"] = float(d.median())
+        err[nm + "_p99"] = float(torch.quantile(d[: 1 << 20].float(), 0.99))
+    t_exact = _time(lambda: m.update(em), 10, st)
+    t_sur = _time(lambda: sur.infer_into(em, o, f, mk, exact_fallback=False), 10, st)
+    t_all = _time(lambda: sur.infer_into(em, o, f, mk), 10, st)
+    rows["surrogate_400x400x72"] = {
+        "train_patches": args.sur_patches, "train_s": train_s, "loss_first": losses[0][1], "loss_last": losses[-1][1],
+        "engine": "tcgen05", "fallback_frac": float(mk.float().mean()), "error_vs_exact_on_surrogate_cells": err,
+        "exact_rebuild_ms": t_exact, "surrogate_only_ms": t_sur, "surrogate_with_fallback_ms": t_all,
+        "gain_vs_exact": t_exact / t_all}
+    return rows
 
 
 def run_e2e(seb, m, world_np, origins, args, dev):

@@ -65,6 +65,9 @@ void launch_defaults(const seb_params& p, const Tables& T, Launch* L) {
   L->kappa_max = p.kappa_max;
   L->phi_x_max = p.phi_x_max;
   L->phi_y_max = p.phi_y_max;
+  L->inv_kappa_max = 1.f / p.kappa_max;
+  L->inv_phi_x_max = 1.f / p.phi_x_max;
+  L->inv_phi_y_max = 1.f / p.phi_y_max;
   L->w0 = p.w[0];
   L->w1 = p.w[1];
   L->w2 = p.w[2];

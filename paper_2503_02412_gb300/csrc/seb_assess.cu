@@ -45,7 +45,8 @@ __device__ __noinline__ Cell finish_cell(int N, int MX, int MY, int MXX, int MXY
   }
   const float res = L.res;
   const float fN = (float)N;
-  const float inv_n2 = 1.f / (fN * fN);
+  const float iN = 1.f / fN;
+  const float inv_n2 = iN * iN;
   // N^2 Cov_xy-block numerators are exact integers (int32 when the tables allow it: 64-bit
   // integer conversions run on the FP64 unit).
   float nxx, nxy, nyy;
@@ -59,15 +60,16 @@ __device__ __noinline__ Cell finish_cell(int N, int MX, int MY, int MXX, int MXY
     nyy = (float)((long long)N * MYY - (long long)MY * MY);
   }
   const float fMX = (float)MX, fMY = (float)MY;
+  const float rr2 = inv_n2 * res * res, rr1 = inv_n2 * res;
   float c[6];
-  c[0] = nxx * inv_n2 * res * res;
-  c[1] = nxy * inv_n2 * res * res;
-  c[3] = nyy * inv_n2 * res * res;
-  c[2] = fmaf(S1, fN, -fMX * S0) * inv_n2 * res;
-  c[4] = fmaf(S2, fN, -fMY * S0) * inv_n2 * res;
+  c[0] = nxx * rr2;
+  c[1] = nxy * rr2;
+  c[3] = nyy * rr2;
+  c[2] = fmaf(S1, fN, -fMX * S0) * rr1;
+  c[4] = fmaf(S2, fN, -fMY * S0) * rr1;
   c[5] = fmaf(S3, fN, -S0 * S0) * inv_n2;
   float n[3], gap;
-  min_eigpair<float>(c, n, &gap);
+  min_eigpair_f(c, n, &gap);
   uint32_t flags = 0;
   const float tr = c[0] + c[3] + c[5];
   if (gap < L.gap_fp64) {
@@ -91,13 +93,16 @@ __device__ __noinline__ Cell finish_cell(int N, int MX, int MY, int MXX, int MXY
     atomicAdd(&L.counters[0], 1ull);
     if (gd < 1e-12) flags |= SEB_FLAG_DEGENERATE;
   } else {
-    o.rough = refine_min<float>(c, n) / tr;
+    // The closed-form eigenvalue is accurate to ~eps * trace; below a relative gap of 0.05 one
+    // Rayleigh-quotient refinement keeps the normal within 1e-5 rad.
+    const float lam = gap < 0.05f ? refine_min<float>(c, n) : fmaxf(rayleigh<float>(c, n), 0.f);
+    o.rough = lam / tr;
   }
   // Body frame (Eqs. 2-3): u = z_b x x_yaw = (-n_z s, n_z c, n_x s - n_y c),
   // y_b = u / |u|, x_b = y_b x z_b, so b3^T x_b = -n_z (n_x c + n_y s) / |u|.
   const float uz = n[0] * st - n[1] * ct;
-  const float un = sqrtf(n[2] * n[2] + uz * uz);
-  if (!(n[2] > 1e-6f) || !(un >= 1e-6f)) flags |= SEB_FLAG_DEGENERATE;
+  const float un2 = n[2] * n[2] + uz * uz;
+  if (!(n[2] > 1e-6f) || !(un2 >= 1e-12f)) flags |= SEB_FLAG_DEGENERATE;
   if (flags & SEB_FLAG_DEGENERATE) {
     o.z = o.pitch = o.roll = qnan;
     o.risk = 1.f;
@@ -105,19 +110,19 @@ __device__ __noinline__ Cell finish_cell(int N, int MX, int MY, int MXX, int MXY
     atomicAdd(&L.counters[1], 1ull);
     return o;
   }
-  const float ybz = fminf(fmaxf(uz / un, -1.f), 1.f);
-  const float xbz = fminf(fmaxf(-n[2] * (n[0] * ct + n[1] * st) / un, -1.f), 1.f);
+  const float iun = rsqrtf(un2);
+  const float ybz = fminf(fmaxf(uz * iun, -1.f), 1.f);
+  const float xbz = fminf(fmaxf(-n[2] * (n[0] * ct + n[1] * st) * iun, -1.f), 1.f);
   o.pitch = asinf(xbz);
   o.roll = asinf(ybz);
   // Plane through the mean with normal n, evaluated at the cell centre (offset 0).
-  const float mz = S0 / fN;
-  o.z = ref + mz + (n[0] * (fMX / fN) + n[1] * (fMY / fN)) * res / n[2];
+  o.z = ref + S0 * iN + (n[0] * fMX + n[1] * fMY) * iN * res / n[2];
   const float ap = fabsf(o.pitch), ar = fabsf(o.roll);
   if (o.rough > L.kappa_max || ap > L.phi_x_max || ar > L.phi_y_max) {
     o.risk = 1.f;
     flags |= SEB_FLAG_OBSTACLE;
   } else {
-    o.risk = L.w0 * (o.rough / L.kappa_max) + L.w1 * (ap / L.phi_x_max) + L.w2 * (ar / L.phi_y_max);
+    o.risk = L.w0 * (o.rough * L.inv_kappa_max) + L.w1 * (ap * L.inv_phi_x_max) + L.w2 * (ar * L.inv_phi_y_max);
   }
   o.flags = flags;
   return o;

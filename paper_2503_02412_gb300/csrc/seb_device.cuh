@@ -181,4 +181,56 @@ __device__ __forceinline__ F refine_min(const F c[6], F n[3]) {
   return l > F(0) ? l : F(0);
 }
 
+// FP32 smallest eigenpair with the same closed form, arranged for throughput: one acos and
+// one sincos (cos(phi + 2 pi / 3) = -cos(phi) / 2 - sqrt(3) sin(phi) / 2), and a reciprocal
+// square root for the normalisation.  Returns the relative gap in *gap_rel.
+__device__ __forceinline__ void min_eigpair_f(const float c[6], float n[3], float* gap_rel) {
+  const float tr = c[0] + c[3] + c[5];
+  const float q = tr * (1.f / 3.f);
+  const float bxx = c[0] - q, byy = c[3] - q, bzz = c[5] - q;
+  const float off = c[1] * c[1] + c[2] * c[2] + c[4] * c[4];
+  const float p2 = (bxx * bxx + byy * byy + bzz * bzz + 2.f * off) * (1.f / 6.f);
+  n[0] = n[1] = 0.f;
+  n[2] = 1.f;
+  *gap_rel = 0.f;
+  if (!(p2 > 0.f) || !(tr > 0.f)) return;
+  const float p = sqrtf(p2);
+  const float det = bxx * (byy * bzz - c[4] * c[4]) - c[1] * (c[1] * bzz - c[4] * c[2]) +
+                    c[2] * (c[1] * c[4] - byy * c[2]);
+  float r = det / (2.f * p2 * p);
+  r = fminf(fmaxf(r, -1.f), 1.f);
+  float sp, cp;
+  sincosf(acosf(r) * (1.f / 3.f), &sp, &cp);
+  const float lmin = q + 2.f * p * (-0.5f * cp - 0.86602540378443865f * sp);
+  *gap_rel = 3.4641016151377546f * p * sp / tr;
+  const float r0[3] = {c[0] - lmin, c[1], c[2]};
+  const float r1[3] = {c[1], c[3] - lmin, c[4]};
+  const float r2[3] = {c[2], c[4], c[5] - lmin};
+  float a[3], b[3], d[3];
+  cross(r0, r1, a);
+  cross(r0, r2, b);
+  cross(r1, r2, d);
+  const float na = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+  const float nb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+  const float nd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  const float* v = a;
+  float m = na;
+  if (nb > m) {
+    v = b;
+    m = nb;
+  }
+  if (nd > m) {
+    v = d;
+    m = nd;
+  }
+  if (!(m > 0.f)) {
+    *gap_rel = 0.f;
+    return;
+  }
+  const float inv = (v[2] < 0.f ? -1.f : 1.f) * rsqrtf(m);
+  n[0] = v[0] * inv;
+  n[1] = v[1] * inv;
+  n[2] = v[2] * inv;
+}
+
 }  // namespace seb

@@ -53,6 +53,7 @@ struct Launch {
   int32_t n_yaw;
   float res;
   float kappa_max, phi_x_max, phi_y_max;
+  float inv_kappa_max, inv_phi_x_max, inv_phi_y_max;
   float w0, w1, w2;
   float gap_fp64;
   int32_t narrow_moments;  // N * sum di^2 etc. fit in int32
