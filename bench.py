@@ -37,7 +37,22 @@ WORKLOAD = "se2_map_400x400x72_rebuild_plus_50_shifts"
 
 # ncu DRAM traffic of one full-map rebuild launch (dram__bytes_read.sum + dram__bytes_write.sum),
 # valid only for the kernel source it was captured on (hash of the assess kernel's sources).
-NCU_TRAFFIC = {"sources_sha": "8433f9d5e817c422", "bytes": 39397376 + 222850048}
+NCU_TRAFFIC = {"sources_sha": "72d78832bd91b77e", "bytes": 26539008 + 210844928}
+
+
+def sliding_flop_per_cell(table):
+    """Algorithmic FP32 FLOP of one cell and one yaw pair in the sliding-row-sum formulation
+    (an FMA counts 2).  Per row run of length n the first column of a 4-column block sums n
+    points (z - ref, A, B, C: 6 FLOP each); the other 3 columns slide the run by one cell
+    (two new z' and 12 FLOP for A, B, C and the column's B: 14 each); each column then adds
+    its run sums to S0..S3 (5).  Per cell: 1.5 N + 15.5 R, with N points and R runs, plus ~200
+    for the eigen-solve, frame and risk of the pair."""
+    t = np.asarray(table)
+    runs = 0
+    for dj in np.unique(t[:, 1]):
+        di = np.sort(t[t[:, 1] == dj, 0])
+        runs += 1 + int(np.count_nonzero(np.diff(di) > 1))
+    return 1.5 * len(t) + 15.5 * runs + 200
 
 
 def kernel_sources_sha():
@@ -296,8 +311,7 @@ def main():
     # roofline of the dominant kernel (the full-map rebuild launch)
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
-    sizes = [len(abi.seb_footprint_table(params.c(), k)) for k in range(K // 2)]
-    flop = NX * NY * sum(9 * n + 200 for n in sizes)  # algorithmic FLOP per rebuild (yaw pairs)
+    flop = NX * NY * sum(sliding_flop_per_cell(abi.seb_footprint_table(params.c(), k)) for k in range(K // 2))
     rb = float(np.mean(rebuild_ms))
     achieved = flop / (rb * 1e-3) / 1e12
     peak = sms * 128 * 2 * 2070e6 / 1e12  # FP32 lanes x FMA x max SM clock
@@ -320,7 +334,8 @@ def main():
         "shift_us_mean": (ms_per_step - rb) / N_SHIFTS * 1e3,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "assess_kernel_sl<float> (rebuild)",
-                     "flop_per_launch": flop, "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+                     "flop_per_launch": flop, "flop_basis": "sliding row sums: 1.5 N + 15.5 R + 200 per cell and yaw pair",
+                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x 2070 MHz"},
         "gpu_launches": launches, "fp64_solves": n64, "degenerate": ndeg, "clocks": clk,
     }
     if e2e is not None:

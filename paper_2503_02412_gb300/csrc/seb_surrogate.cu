@@ -636,11 +636,11 @@ __global__ void __launch_bounds__(128) map_head_kernel(const bf16* __restrict__ 
                                                        const float* __restrict__ bh, const float* __restrict__ elev,
                                                        int nx, int ny, int n_yaw, float* __restrict__ out,
                                                        uint8_t* __restrict__ flags) {
+  // one thread per cell: its 32 activations once in registers, all 4 x n_pairs outputs
+  extern __shared__ float hw[];  // [nout][kHid] weights, then [nout] biases
   const int npairs = n_yaw / 2, nout = 4 * npairs;
-  const int k = blockIdx.y;  // yaw pair
-  __shared__ float ws[4 * kHid + 4];
-  for (int i = threadIdx.x; i < 4 * kHid; i += blockDim.x) ws[i] = __bfloat162float(wh[(int64_t)4 * k * kHid + i]);
-  if (threadIdx.x < 4) ws[4 * kHid + threadIdx.x] = bh[4 * k + threadIdx.x];
+  for (int i = threadIdx.x; i < nout * kHid; i += blockDim.x) hw[i] = __bfloat162float(wh[i]);
+  for (int i = threadIdx.x; i < nout; i += blockDim.x) hw[nout * kHid + i] = bh[i];
   __syncthreads();
   const int W4 = nx - 2 * kMargin, H4 = ny - 2 * kMargin;
   const int64_t plane = (int64_t)nx * ny, chs = plane * n_yaw;
@@ -648,35 +648,49 @@ __global__ void __launch_bounds__(128) map_head_kernel(const bf16* __restrict__ 
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < (int64_t)W4 * H4;
        p += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(p / W4), j = (int)(p - (int64_t)i * W4);
-    const int r = i + kMargin, c = j + kMargin;
-    float q[4];
+    const int64_t cell = (int64_t)(i + kMargin) * nx + j + kMargin;
+    float av[kHid];
+    const uint4* ap = reinterpret_cast<const uint4*>(a + p * kHid);
 #pragma unroll
-    for (int t = 0; t < 4; ++t) q[t] = ws[4 * kHid + t];
+    for (int q = 0; q < kHid / 8; ++q) {
+      const uint4 v = ap[q];
+      const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&v);
 #pragma unroll
-    for (int cc = 0; cc < kHid; ++cc) {
-      const float av = __bfloat162float(a[p * kHid + cc]);
-#pragma unroll
-      for (int t = 0; t < 4; ++t) q[t] = fmaf(ws[t * kHid + cc], av, q[t]);
+      for (int t = 0; t < 4; ++t) {
+        const float2 f = __bfloat1622float2(h2[t]);
+        av[8 * q + 2 * t] = f.x;
+        av[8 * q + 2 * t + 1] = f.y;
+      }
     }
-    const int64_t cell = (int64_t)r * nx + c;
-    const float z = elev[cell] + q[0] / kZScale;
-    const float risk = fminf(fmaxf(q[3], 0.f), 1.f);
-    const uint8_t f = (uint8_t)(SEB_FLAG_SURROGATE | (risk >= 1.f ? SEB_FLAG_OBSTACLE : 0));
-    const int64_t i0 = (int64_t)k * plane + cell, i1 = (int64_t)(k + npairs) * plane + cell;
-    out[i0] = z;
-    out[i1] = z;
-    out[chs + i0] = q[1];
-    out[chs + i1] = -q[1];
-    out[2 * chs + i0] = q[2];
-    out[2 * chs + i1] = -q[2];
-    out[3 * chs + i0] = qnan;
-    out[3 * chs + i1] = qnan;
-    out[4 * chs + i0] = risk;
-    out[4 * chs + i1] = risk;
-    flags[i0] = f;
-    flags[i1] = f;
+    const float ez = elev[cell];
+    for (int k = 0; k < npairs; ++k) {
+      float qv[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const float* w = hw + (4 * k + t) * kHid;
+        float s = hw[nout * kHid + 4 * k + t];
+#pragma unroll
+        for (int c = 0; c < kHid; ++c) s = fmaf(w[c], av[c], s);
+        qv[t] = s;
+      }
+      const float z = ez + qv[0] / kZScale;
+      const float risk = fminf(fmaxf(qv[3], 0.f), 1.f);
+      const uint8_t f = (uint8_t)(SEB_FLAG_SURROGATE | (risk >= 1.f ? SEB_FLAG_OBSTACLE : 0));
+      const int64_t i0 = (int64_t)k * plane + cell, i1 = (int64_t)(k + npairs) * plane + cell;
+      out[i0] = z;
+      out[i1] = z;
+      out[chs + i0] = qv[1];
+      out[chs + i1] = -qv[1];
+      out[2 * chs + i0] = qv[2];
+      out[2 * chs + i1] = -qv[2];
+      out[3 * chs + i0] = qnan;
+      out[3 * chs + i1] = qnan;
+      out[4 * chs + i0] = risk;
+      out[4 * chs + i1] = risk;
+      flags[i0] = f;
+      flags[i1] = f;
+    }
   }
-  (void)nout;
 }
 
 // Fallback mask: a cell goes to the exact kernel when an unknown cell or a step edge (a
@@ -1056,8 +1070,12 @@ int seb_sur_infer(seb_sur* h, const float* elev, float step, int32_t radius, int
     H -= 2 * kDil[l];
     x = y;
   }
-  map_head_kernel<<<dim3(grid_for((int64_t)W * H, 128), h->p.n_yaw / 2), 128, 0, st>>>(
-      x, wb + h->PL.wh, master + h->PL.bh, elev, nx, ny, h->p.n_yaw, out, flags);
+  {
+    const size_t shm = (size_t)h->nout * (kHid + 1) * sizeof(float);
+    cudaFuncSetAttribute(map_head_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    map_head_kernel<<<grid_for((int64_t)W * H, 128), 128, shm, st>>>(x, wb + h->PL.wh, master + h->PL.bh, elev, nx,
+                                                                      ny, h->p.n_yaw, out, flags);
+  }
   uint8_t* mask = mask_out ? mask_out : at<uint8_t>(h, h->v.mask);
   uint8_t* tiles = at<uint8_t>(h, h->v.tiles);
   const int tx = (nx + 31) / 32, ty = (ny + 31) / 32;
