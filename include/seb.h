@@ -147,7 +147,9 @@ int seb_map_set_stream(seb_map* m, seb_stream_t stream);
 /*
  * Full rebuild (Algorithm 1 for every SE(2) cell).  elev_dev: device [ny][nx] in the map's
  * elev_dtype, logical order, at least 16-byte aligned; read only during the call's kernels.
- * (origin_i, origin_j): grid index of the window origin.  Resets the ring offsets to 0.
+ * (origin_i, origin_j): grid index of the window origin.  Sets the ring offsets to the origin
+ * modulo the map size, so that a cell's physical row and column are its grid indices modulo
+ * (ny, nx) for the whole life of the map (a rolling map over a torus, Sec. V-A).
  */
 int seb_map_update(seb_map* m, const void* elev_dev, int64_t origin_i, int64_t origin_j);
 

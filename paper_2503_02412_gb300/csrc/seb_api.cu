@@ -210,7 +210,10 @@ int seb_map_update(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
   if (!m) return fail(nullptr, SEB_ERR_INVALID_ARG, "map is NULL");
   int rc = check_elev(m, elev);
   if (rc) return rc;
-  m->ring_x = m->ring_y = 0;
+  // physical index = grid index mod n (the window's torus), so that a rebuild and any later
+  // shift see the same physical alignment of the globally aligned cell blocks
+  m->ring_x = (int32_t)(((oi % m->p.nx) + m->p.nx) % m->p.nx);
+  m->ring_y = (int32_t)(((oj % m->p.ny) + m->p.ny) % m->p.ny);
   Launch L = base_launch(m, elev);
   launch_set_origin(L, oi, oj);
   launch_request(L, 0, 0, m->p.nx, m->p.ny);

@@ -45,7 +45,7 @@ __device__ __noinline__ Cell finish_cell(int N, int MX, int MY, int MXX, int MXY
   }
   const float res = L.res;
   const float fN = (float)N;
-  const float iN = 1.f / fN;
+  const float iN = 1.f / fN;  // exact reciprocal: the means use it
   const float inv_n2 = iN * iN;
   // N^2 Cov_xy-block numerators are exact integers (int32 when the tables allow it: 64-bit
   // integer conversions run on the FP64 unit).
@@ -96,7 +96,7 @@ __device__ __noinline__ Cell finish_cell(int N, int MX, int MY, int MXX, int MXY
     // The closed-form eigenvalue is accurate to ~eps * trace; below a relative gap of 0.05 one
     // Rayleigh-quotient refinement keeps the normal within 1e-5 rad.
     const float lam = gap < 0.05f ? refine_min<float>(c, n) : fmaxf(rayleigh<float>(c, n), 0.f);
-    o.rough = lam / tr;
+    o.rough = __fdividef(lam, tr);  // 2-ulp division: far inside the 1e-4 bar
   }
   // Body frame (Eqs. 2-3): u = z_b x x_yaw = (-n_z s, n_z c, n_x s - n_y c),
   // y_b = u / |u|, x_b = y_b x z_b, so b3^T x_b = -n_z (n_x c + n_y s) / |u|.
@@ -116,7 +116,7 @@ __device__ __noinline__ Cell finish_cell(int N, int MX, int MY, int MXX, int MXY
   o.pitch = asinf(xbz);
   o.roll = asinf(ybz);
   // Plane through the mean with normal n, evaluated at the cell centre (offset 0).
-  o.z = ref + S0 * iN + (n[0] * fMX + n[1] * fMY) * iN * res / n[2];
+  o.z = ref + S0 * iN + (n[0] * fMX + n[1] * fMY) * iN * res * __fdividef(1.f, n[2]);
   const float ap = fabsf(o.pitch), ar = fabsf(o.roll);
   if (o.rough > L.kappa_max || ap > L.phi_x_max || ar > L.phi_y_max) {
     o.risk = 1.f;
@@ -465,12 +465,13 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int lx = 4 * cb, ly = 2 * rp;
   const int cx = tx0 + lx, cy = ty0 + ly;
   auto stores = [&](int c, int r) { return c >= R.x0 && c < R.x0 + R.w && r >= R.y0 && r < R.y0 + R.h; };
-  if (L.store_mask) {
-    // masked-store launch: a warp without a cell to store skips the work (warp-uniform)
+  {
+    // a warp without a cell to store (outside the rectangle, or masked out) skips the work;
+    // no block-wide barrier follows
     int need = 0;
     for (int h = 0; h < 2; ++h)
       for (int g = 0; g < 4; ++g)
-        if (stores(cx + g, cy + h) && L.store_mask[(int64_t)(cy + h) * L.nx + cx + g]) need = 1;
+        if (stores(cx + g, cy + h) && (!L.store_mask || L.store_mask[(int64_t)(cy + h) * L.nx + cx + g])) need = 1;
     if (!__any_sync(0xffffffffu, need)) return;
   }
   const int pair = blockIdx.y;
@@ -604,35 +605,66 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int r = cy + h;
     int pr = r + L.ring_y;
     if (pr >= L.ny) pr -= L.ny;
+    Cell o[4];
+    bool keep[4];
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
       const int c = cx + g;
-      if (!stores(c, r)) continue;
-      if (L.store_mask && !L.store_mask[(int64_t)r * L.nx + c]) continue;
+      keep[g] = stores(c, r) && (!L.store_mask || L.store_mask[(int64_t)r * L.nx + c]);
+      if (!keep[g]) continue;
       float qv[6];
 #pragma unroll
       for (int k = 0; k < 6; ++k) qv[k] = h ? Qs(k, g).y : Qs(k, g).x;
-      const Cell o = finish_cell(mom[0] - (int)qv[0], mom[1] - (int)qv[1], mom[2] - (int)qv[2], mom[3] - (int)qv[3],
-                                 mom[4] - (int)qv[4], mom[5] - (int)qv[5], h ? S0[g].y : S0[g].x,
-                                 h ? S1[g].y : S1[g].x, h ? S2[g].y : S2[g].x, h ? S3[g].y : S3[g].x, ref,
-                                 T.n_min[pair], ct, st, L);
-      int pc = c + L.ring_x;
-      if (pc >= L.nx) pc -= L.nx;
+      o[g] = finish_cell(mom[0] - (int)qv[0], mom[1] - (int)qv[1], mom[2] - (int)qv[2], mom[3] - (int)qv[3],
+                         mom[4] - (int)qv[4], mom[5] - (int)qv[5], h ? S0[g].y : S0[g].x, h ? S1[g].y : S1[g].x,
+                         h ? S2[g].y : S2[g].x, h ? S3[g].y : S3[g].x, ref, T.n_min[pair], ct, st, L);
+    }
+    int pc = cx + L.ring_x;
+    if (pc >= L.nx) pc -= L.nx;
+    float* out = L.out;
+    if (L.vec4 && keep[0] && keep[1] && keep[2] && keep[3] && (pc & 3) == 0) {
+      // the block's 4 cells are 4 consecutive, 16-byte aligned physical cells (nx % 4 == 0,
+      // so no ring wrap falls inside it): one 16-byte store per channel and plane
       const int64_t i0 = (int64_t)k0 * L.plane + (int64_t)pr * L.nx + pc;
       const int64_t i1 = (int64_t)k1 * L.plane + (int64_t)pr * L.nx + pc;
-      float* out = L.out;
-      out[i0] = o.z;
-      out[i1] = o.z;
-      out[chs + i0] = o.pitch;
-      out[chs + i1] = -o.pitch;
-      out[2 * chs + i0] = o.roll;
-      out[2 * chs + i1] = -o.roll;
-      out[3 * chs + i0] = o.rough;
-      out[3 * chs + i1] = o.rough;
-      out[4 * chs + i0] = o.risk;
-      out[4 * chs + i1] = o.risk;
-      L.flags[i0] = (uint8_t)o.flags;
-      L.flags[i1] = (uint8_t)o.flags;
+      auto st4 = [&](int64_t i, float a, float b, float c, float d) {
+        *reinterpret_cast<float4*>(out + i) = make_float4(a, b, c, d);
+      };
+      st4(i0, o[0].z, o[1].z, o[2].z, o[3].z);
+      st4(i1, o[0].z, o[1].z, o[2].z, o[3].z);
+      st4(chs + i0, o[0].pitch, o[1].pitch, o[2].pitch, o[3].pitch);
+      st4(chs + i1, -o[0].pitch, -o[1].pitch, -o[2].pitch, -o[3].pitch);
+      st4(2 * chs + i0, o[0].roll, o[1].roll, o[2].roll, o[3].roll);
+      st4(2 * chs + i1, -o[0].roll, -o[1].roll, -o[2].roll, -o[3].roll);
+      st4(3 * chs + i0, o[0].rough, o[1].rough, o[2].rough, o[3].rough);
+      st4(3 * chs + i1, o[0].rough, o[1].rough, o[2].rough, o[3].rough);
+      st4(4 * chs + i0, o[0].risk, o[1].risk, o[2].risk, o[3].risk);
+      st4(4 * chs + i1, o[0].risk, o[1].risk, o[2].risk, o[3].risk);
+      const uint32_t fw = (o[0].flags & 0xffu) | ((o[1].flags & 0xffu) << 8) | ((o[2].flags & 0xffu) << 16) |
+                          ((o[3].flags & 0xffu) << 24);  // little-endian: byte g is cell g
+      *reinterpret_cast<uint32_t*>(L.flags + i0) = fw;
+      *reinterpret_cast<uint32_t*>(L.flags + i1) = fw;
+      continue;
+    }
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      if (!keep[g]) continue;
+      int pcg = pc + g;
+      if (pcg >= L.nx) pcg -= L.nx;
+      const int64_t i0 = (int64_t)k0 * L.plane + (int64_t)pr * L.nx + pcg;
+      const int64_t i1 = (int64_t)k1 * L.plane + (int64_t)pr * L.nx + pcg;
+      out[i0] = o[g].z;
+      out[i1] = o[g].z;
+      out[chs + i0] = o[g].pitch;
+      out[chs + i1] = -o[g].pitch;
+      out[2 * chs + i0] = o[g].roll;
+      out[2 * chs + i1] = -o[g].roll;
+      out[3 * chs + i0] = o[g].rough;
+      out[3 * chs + i1] = o[g].rough;
+      out[4 * chs + i0] = o[g].risk;
+      out[4 * chs + i1] = o[g].risk;
+      L.flags[i0] = (uint8_t)o[g].flags;
+      L.flags[i1] = (uint8_t)o[g].flags;
     }
   }
 }
@@ -730,6 +762,9 @@ cudaError_t launch_typed(const Tables& T, const Launch& Lreq, cudaStream_t strea
   Launch L = Lreq;
   if (!COMP) {
     decompose_sl(L);
+    // 16-byte stores of whole cell blocks need 4 | nx (no ring wrap inside a block) and
+    // aligned output planes
+    L.vec4 = (L.nx % 4 == 0) && ((uintptr_t)L.out % 16 == 0) && ((uintptr_t)L.flags % 4 == 0);
     const size_t smem = smem_sl(T, L);
     if (smem <= 227 * 1024) {
       if (L.tile_start[L.n_rects] == 0) return cudaSuccess;

@@ -197,12 +197,12 @@ __device__ __forceinline__ void min_eigpair_f(const float c[6], float n[3], floa
   const float p = sqrtf(p2);
   const float det = bxx * (byy * bzz - c[4] * c[4]) - c[1] * (c[1] * bzz - c[4] * c[2]) +
                     c[2] * (c[1] * c[4] - byy * c[2]);
-  float r = det / (2.f * p2 * p);
+  float r = __fdividef(det, 2.f * p2 * p);  // clamped below; a 2-ulp quotient is ample
   r = fminf(fmaxf(r, -1.f), 1.f);
   float sp, cp;
   sincosf(acosf(r) * (1.f / 3.f), &sp, &cp);
   const float lmin = q + 2.f * p * (-0.5f * cp - 0.86602540378443865f * sp);
-  *gap_rel = 3.4641016151377546f * p * sp / tr;
+  *gap_rel = __fdividef(3.4641016151377546f * p * sp, tr);
   const float r0[3] = {c[0] - lmin, c[1], c[2]};
   const float r1[3] = {c[1], c[3] - lmin, c[4]};
   const float r2[3] = {c[2], c[4], c[5] - lmin};

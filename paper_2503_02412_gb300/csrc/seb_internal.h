@@ -60,6 +60,7 @@ struct Launch {
   int32_t n_req;          // rectangles of cells to recompute, before tiling
   Rect req[4];
   int32_t phase_x, phase_y;  // window origin mod 4 / mod 2 (global alignment of cell blocks)
+  int32_t vec4;              // whole 4-cell blocks may be stored with 16-byte stores
   int32_t n_rects;
   Rect rects[kMaxRects];
   int32_t tile_start[kMaxRects + 1];
