@@ -395,7 +395,31 @@ def measure_rows(seb, args, dev):
     tf, tb = _time(fwd, 10, st), _time(bwd, 10, st)
     rows["query_1M_poses"] = {"fwd_ms": tf, "bwd_ms": tb, "fwd_poses_per_s": n / tf * 1e3,
                               "bwd_poses_per_s": n / tb * 1e3, "config": "100x100 map at 0.1 m, 0.6x0.4 m"}
-    del poses, out, fl, sv, g, gp
+    # trilinear SE(2) lookup of the grid at the same poses, against the exact query
+    abi.seb_query_poses(c, e.data_ptr(), 0, 0, poses.data_ptr(), n, out.data_ptr(), fl.data_ptr(), 0, st.cuda_stream)
+    mq = seb.SebMap(pq, dev)
+    mq.update(e)
+    val = torch.empty(n, device=dev)
+    grad = torch.empty(n, 3, device=dev)
+    lfl = torch.empty(n, dtype=torch.uint8, device=dev)
+    gv = torch.randn(n, device=dev)
+    grids = [abi.seb_map_grid(mq.handle, ch) for ch in range(5)]
+    lk = lambda: abi.seb_se2_lookup(grids[4], poses.data_ptr(), n, 1.0, val.data_ptr(), grad.data_ptr(),  # noqa: E731
+                                    lfl.data_ptr(), st.cuda_stream)
+    lkv = lambda: abi.seb_se2_lookup_vjp(grids[4], poses.data_ptr(), n, gv.data_ptr(), gp.data_ptr(),  # noqa: E731
+                                         st.cuda_stream)
+    tl, tv = _time(lk, 20, st), _time(lkv, 20, st)
+    err = {}
+    known = fl == 0
+    for ch, name in ((0, "z"), (1, "pitch"), (2, "roll"), (4, "risk")):
+        abi.seb_se2_lookup(grids[ch], poses.data_ptr(), n, float("nan"), val.data_ptr(), None, None, st.cuda_stream)
+        d = (val - out[:, ch]).abs()[known & torch.isfinite(val)]
+        err[f"{name}_p50"] = float(d.quantile(0.5)) if d.numel() else None
+        err[f"{name}_p99"] = float(d.quantile(0.99)) if d.numel() else None
+    rows["lookup_1M_poses"] = {"value_grad_ms": tl, "vjp_ms": tv, "poses_per_s": n / tl * 1e3,
+                               "vs_exact_query_fwd": tf / tl, "error_vs_exact_query": err,
+                               "config": "risk channel of the 100x100x36 map at the query's poses"}
+    del poses, out, fl, sv, g, gp, val, grad, lfl, gv, mq
     # S8
     e3 = torch.from_numpy(bumpy_plane(21, 1024, 1024, 0.05)).to(dev)
     prec = {}

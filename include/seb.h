@@ -207,6 +207,49 @@ int seb_query_poses_backward(const seb_params* p, const void* elev_dev, int64_t 
                              seb_stream_t stream);
 
 /*
+ * SE(2) grid lookup (Sec. VI: the planner reads Risk and the signed distance field at
+ * continuous states by trilinear interpolation of the grid, with the yaw handled on SO(2)).
+ * A seb_grid names one float32 channel [n_yaw][ny][nx] on the device, ring-indexed like the
+ * map's outputs: the value of cell (c, r) and yaw bin k sits at world
+ * ((origin_i + c + 1/2) res, (origin_j + r + 1/2) res, 2 pi k / n_yaw) and is stored at
+ * data[k][(r + ring_y) mod ny][(c + ring_x) mod nx].  The grid is read, never written.
+ */
+typedef struct {
+  const float* data;
+  int32_t nx, ny, n_yaw;
+  int32_t ring_x, ring_y;
+  int64_t origin_i, origin_j;
+  float res;
+} seb_grid;
+
+/* Fills g with output channel `channel` (0..SEB_N_CH-1: z, pitch, roll, roughness, risk) of
+ * the map; valid until the map's next update or shift.  SEB_ERR_INVALID_ARG before the first
+ * update or for a bad channel. */
+int seb_map_grid(const seb_map* m, int32_t channel, seb_grid* g);
+
+/*
+ * Trilinear lookup at poses_dev [n][3] (x, y, yaw in world metres / radians):
+ *   u = x / res - origin_i - 1/2,  v = y / res - origin_j - 1/2,  w = yaw n_yaw / (2 pi)
+ *   reduced to [0, n_yaw).  A pose is inside when 0 <= u <= nx - 1 and 0 <= v <= ny - 1.
+ *   Its cell is (c0, r0) = (min(floor u, nx - 2), min(floor v, ny - 2)) and its yaw bins are
+ *   k0 = floor w, k1 = (k0 + 1) mod n_yaw (the SO(2) wrap).  The value blends the 8 corners
+ *   with weights (1 - a or a)(1 - b or b)(1 - t or t), a = u - c0, b = v - r0, t = w - k0;
+ *   the gradient is the derivative of the same blend in world units (d/dx, d/dy, d/dyaw).
+ * val_dev [n] is required; grad_dev [n][3] and flags_dev [n] may be NULL.  Outside the window:
+ * value `fill`, gradient 0 and SEB_FLAG_UNKNOWN; a NaN value (an unknown corner) also sets
+ * SEB_FLAG_UNKNOWN.  A pose with a non-finite coordinate or |yaw| > 1e4 rad counts as outside.
+ * Needs nx, ny >= 2 and 1 <= n_yaw <= 4096 (else SEB_ERR_BAD_SHAPE); poses are read once, no
+ * state is kept.
+ */
+int seb_se2_lookup(const seb_grid* g, const float* poses_dev, int64_t n, float fill, float* val_dev,
+                   float* grad_dev, uint8_t* flags_dev, seb_stream_t stream);
+
+/* Adjoint of seb_se2_lookup: grad_pose_dev [n][3] = grad_val_dev[i] * d value_i / d pose_i
+ * (0 outside the window). */
+int seb_se2_lookup_vjp(const seb_grid* g, const float* poses_dev, int64_t n, const float* grad_val_dev,
+                       float* grad_pose_dev, seb_stream_t stream);
+
+/*
  * Learned surrogate (not in the paper, which names learned traversability as less reliable
  * than geometry, Sec. II-A): a BF16 convolutional network predicting, per cell and yaw pair,
  * (z - z_cell, pitch, roll, risk) of the assessment above from an elevation patch.  Slope

@@ -19,7 +19,9 @@ states by trilinear interpolation of the SE(2) grid, with the yaw handled on SO(
 * The value is the sum over the 8 corners of ``(1 - a or a)(1 - b or b)(1 - t or t) V``.
   The gradient is the derivative of that same trilinear form, scaled to world units:
   ``(d/du / res, d/dv / res, d/dw K / (2 pi))``.
-* Outside: value ``fill``, gradient 0, flag UNKNOWN.  A NaN value also sets UNKNOWN.
+* Outside: value ``fill``, gradient 0, flag UNKNOWN.  A NaN value also sets UNKNOWN.  A pose
+  with a non-finite coordinate or ``|theta| > 1e4`` rad counts as outside (an interface rule of
+  the library, not of the paper).
 
 Pins: ``tests/test_lookup_pins.py`` (grid nodes, exact reproduction of multilinear
 functions, SO(2) periodicity, central differences, scipy's RegularGridInterpolator).
@@ -39,9 +41,9 @@ def se2_lookup(grid, poses, res, origin=(0, 0), ring=(0, 0), fill=np.nan):
     x, y, th = P[:, 0], P[:, 1], P[:, 2]
     u = x / res - origin[0] - 0.5
     v = y / res - origin[1] - 0.5
-    w = th * K / (2.0 * np.pi)
+    w = np.where(np.abs(th) <= 1e4, th, 0.0) * K / (2.0 * np.pi)
     w = w - K * np.floor(w / K)
-    inside = (u >= 0) & (u <= nx - 1) & (v >= 0) & (v <= ny - 1)
+    inside = (u >= 0) & (u <= nx - 1) & (v >= 0) & (v <= ny - 1) & (np.abs(th) <= 1e4)
     uc = np.where(inside, u, 0.0)
     vc = np.where(inside, v, 0.0)
     c0 = np.minimum(np.floor(uc), nx - 2).astype(np.int64)

@@ -48,6 +48,9 @@ EXPORTS = (
     "seb_query_poses",
     "seb_query_poses_backward",
     "seb_query_poses_grad_noalloc",
+    "seb_map_grid",
+    "seb_se2_lookup",
+    "seb_se2_lookup_vjp",
     "seb_sur_workspace_bytes",
     "seb_sur_create",
     "seb_sur_destroy",
@@ -86,6 +89,21 @@ class seb_params(ctypes.Structure):
         ("elev_dtype", ctypes.c_int32),
         ("precision", ctypes.c_int32),
         ("gap_fp64", ctypes.c_float),
+    ]
+
+
+class seb_grid(ctypes.Structure):
+    """One ring-indexed [n_yaw][ny][nx] float32 channel on the device (seb.h)."""
+    _fields_ = [
+        ("data", ctypes.c_void_p),
+        ("nx", ctypes.c_int32),
+        ("ny", ctypes.c_int32),
+        ("n_yaw", ctypes.c_int32),
+        ("ring_x", ctypes.c_int32),
+        ("ring_y", ctypes.c_int32),
+        ("origin_i", ctypes.c_int64),
+        ("origin_j", ctypes.c_int64),
+        ("res", ctypes.c_float),
     ]
 
 
@@ -170,6 +188,9 @@ def load():
             "seb_query_poses": (ctypes.c_int, [P, vp, i64, i64, vp, i64, vp, vp, vp, vp]),
             "seb_query_poses_backward": (ctypes.c_int, [P, vp, i64, i64, vp, vp, vp, vp, i64, vp]),
             "seb_query_poses_grad_noalloc": (ctypes.c_int, [P, vp, i64, i64, vp, i64, vp, vp, vp, vp, vp]),
+            "seb_map_grid": (ctypes.c_int, [vp, i32, ctypes.POINTER(seb_grid)]),
+            "seb_se2_lookup": (ctypes.c_int, [ctypes.POINTER(seb_grid), vp, i64, ctypes.c_float, vp, vp, vp, vp]),
+            "seb_se2_lookup_vjp": (ctypes.c_int, [ctypes.POINTER(seb_grid), vp, i64, vp, vp, vp]),
             "seb_sur_workspace_bytes": (sz, [P, i32]),
             "seb_sur_create": (ctypes.c_int, [P, i32, vp, sz, vp, ctypes.POINTER(vp)]),
             "seb_sur_destroy": (ctypes.c_int, [vp]),
@@ -280,6 +301,20 @@ def seb_query_poses_backward(p: seb_params, elev_ptr, origin_i, origin_j, poses_
                              grad_out_ptr, grad_pose_ptr, n, stream=0) -> None:
     _check(load().seb_query_poses_backward(ctypes.byref(p), elev_ptr, origin_i, origin_j, poses_ptr,
                                            saved_ptr, grad_out_ptr, grad_pose_ptr, n, stream))
+
+
+def seb_map_grid(handle, channel) -> seb_grid:
+    g = seb_grid()
+    _check(load().seb_map_grid(handle, channel, ctypes.byref(g)))
+    return g
+
+
+def seb_se2_lookup(grid: seb_grid, poses_ptr, n, fill, val_ptr, grad_ptr=None, flags_ptr=None, stream=0) -> None:
+    _check(load().seb_se2_lookup(ctypes.byref(grid), poses_ptr, n, fill, val_ptr, grad_ptr, flags_ptr, stream))
+
+
+def seb_se2_lookup_vjp(grid: seb_grid, poses_ptr, n, grad_val_ptr, grad_pose_ptr, stream=0) -> None:
+    _check(load().seb_se2_lookup_vjp(ctypes.byref(grid), poses_ptr, n, grad_val_ptr, grad_pose_ptr, stream))
 
 
 def seb_query_poses_grad_noalloc(p: seb_params, elev_ptr, origin_i, origin_j, poses_ptr, n, grad_out_ptr, out_ptr,

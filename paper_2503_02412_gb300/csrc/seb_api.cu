@@ -280,6 +280,23 @@ int seb_map_shift(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
   return SEB_OK;
 }
 
+int seb_map_grid(const seb_map* m, int32_t channel, seb_grid* g) {
+  if (!m || !g) return fail(nullptr, SEB_ERR_INVALID_ARG, "map or grid is NULL");
+  if (channel < 0 || channel >= SEB_N_CH) return fail(nullptr, SEB_ERR_INVALID_ARG, "channel out of range");
+  if (!m->valid) return fail(nullptr, SEB_ERR_INVALID_ARG, "map has no outputs before its first update");
+  const int64_t plane = (int64_t)m->p.nx * m->p.ny;
+  g->data = m->out + (int64_t)channel * m->p.n_yaw * plane;
+  g->nx = m->p.nx;
+  g->ny = m->p.ny;
+  g->n_yaw = m->p.n_yaw;
+  g->ring_x = m->ring_x;
+  g->ring_y = m->ring_y;
+  g->origin_i = m->oi;
+  g->origin_j = m->oj;
+  g->res = m->p.res;
+  return SEB_OK;
+}
+
 int seb_map_view(const seb_map* m, seb_view* v) {
   if (!m || !v) return fail(nullptr, SEB_ERR_INVALID_ARG, "map or view is NULL");
   v->out = m->out;

@@ -8,6 +8,8 @@ from .terrain import (  # noqa: F401
     bumpy_plane,
     fractal_steps_nan,
     fractal_world,
+    lookup_poses,
+    random_se2_grid,
     shift_sequence,
     random_poses,
     tilted_plane,

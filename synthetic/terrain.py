@@ -136,3 +136,23 @@ def random_poses(seed, n, nx, ny, res, margin_cells, origin=(0, 0), dtype=np.flo
     y = (oj + rng.uniform(margin_cells, ny - margin_cells, size=n)) * res
     th = rng.uniform(0.0, 2 * np.pi, size=n)
     return np.stack([x, y, th], axis=1).astype(dtype)
+
+
+def random_se2_grid(seed, n_yaw, ny, nx, nan_frac=0.0, dtype=np.float32):
+    """A [n_yaw][ny][nx] grid of N(0, 1) values with a fraction of NaN entries."""
+    rng = np.random.default_rng(seed)
+    g = rng.normal(size=(n_yaw, ny, nx))
+    if nan_frac > 0:
+        g[rng.random(g.shape) < nan_frac] = np.nan
+    return g.astype(dtype)
+
+
+def lookup_poses(seed, n, nx, ny, res, origin=(0, 0), pad_cells=2.0, yaw_range=20.0, dtype=np.float32):
+    """Poses [n, 3] spread over the window and pad_cells beyond it (so some fall outside),
+    with yaw uniform in [-yaw_range, yaw_range] (several turns, both signs)."""
+    rng = np.random.default_rng(seed)
+    oi, oj = origin
+    x = (oi + 0.5 + rng.uniform(-pad_cells, nx - 1 + pad_cells, size=n)) * res
+    y = (oj + 0.5 + rng.uniform(-pad_cells, ny - 1 + pad_cells, size=n)) * res
+    th = rng.uniform(-yaw_range, yaw_range, size=n)
+    return np.stack([x, y, th], axis=1).astype(dtype)
