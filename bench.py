@@ -420,6 +420,26 @@ def measure_rows(seb, args, dev):
                                "vs_exact_query_fwd": tf / tl, "error_vs_exact_query": err,
                                "config": "risk channel of the 100x100x36 map at the query's poses"}
     del poses, out, fl, sv, g, gp, val, grad, lfl, gv, mq
+    # signed distance field of the obstacle set of the 400x400x72 map, read back by the lookup
+    mc2 = seb.SebMap(seb.SebParams(nx=NX, ny=NY, n_yaw=K, res=RES, length=LENGTH, width=WIDTH), dev)
+    mc2.update(torch.from_numpy(fractal_steps_nan(0)).to(dev))
+    risk = seb.SE2Grid.from_map(mc2, 4)
+    sdf_t = torch.empty((K, NY, NX), device=dev)
+    work = torch.empty(abi.seb_sdf_workspace_bytes(NX, NY, K), dtype=torch.uint8, device=dev)
+    sdf_grid = seb.risk_sdf(risk, 1.0, 2.0, out=sdf_t, work=work)
+    ts = _time(lambda: seb.risk_sdf(risk, 1.0, 2.0, out=sdf_t, work=work), 20, st)
+    n2 = 1 << 20
+    p2 = torch.from_numpy(random_poses(5, n2, NX, NY, RES, 12)).to(dev)
+    v2 = torch.empty(n2, device=dev)
+    g2 = torch.empty(n2, 3, device=dev)
+    tl2 = _time(lambda: abi.seb_se2_lookup(sdf_grid.g, p2.data_ptr(), n2, 2.0, v2.data_ptr(), g2.data_ptr(), None,
+                                           st.cuda_stream), 20, st)
+    obst = float((sdf_t < 0).float().mean())
+    rows["sdf_400x400x72"] = {"sdf_ms": ts, "cells_per_s": NX * NY * K / ts * 1e3, "obstacle_frac": obst,
+                              "lookup_1M_value_grad_ms": tl2,
+                              "hbm_gbs": 16 * NX * NY * K / ts / 1e6,  # risk in, work out + in, sdf out
+                              "config": "risk channel of the 400x400x72 fractal map, obstacles risk >= 1, clamp 2 m"}
+    del mc2, sdf_t, work, p2, v2, g2, sdf_grid, risk
     # S8
     e3 = torch.from_numpy(bumpy_plane(21, 1024, 1024, 0.05)).to(dev)
     prec = {}

@@ -250,6 +250,24 @@ int seb_se2_lookup_vjp(const seb_grid* g, const float* poses_dev, int64_t n, con
                        float* grad_pose_dev, seb_stream_t stream);
 
 /*
+ * Signed distance field of the obstacle set (Sec. VI: the planner's collision term reads an
+ * SDF over SE(2) whose value at a state is the distance to the edge of the nearest region,
+ * negative inside obstacles; the paper builds it from the risk map).  Per yaw bin, obstacles
+ * are the cells of `risk` with risk >= risk_obstacle (NaN counts as an obstacle; 1 selects
+ * Algorithm 1's explicit obstacles, unknown cells included); distances are Euclidean between
+ * cell centres of that bin's (x, y) plane, in metres, in the window's logical order:
+ *   sdf = res * (distance to the nearest obstacle - distance to the nearest free cell),
+ * clamped to [-clamp, clamp] (clamp >= 0; INFINITY for none; an empty set contributes +inf).
+ * sdf_dev [n_yaw][ny][nx] float32 is written ring-indexed like risk, so a seb_grid with risk's
+ * fields and data = sdf_dev describes it; it may not alias risk.  work_dev: caller-owned,
+ * 4-byte aligned, at least seb_sdf_workspace_bytes(nx, ny, n_yaw) bytes.  Exact (integer)
+ * squared distances; sides up to 16384 cells.
+ */
+size_t seb_sdf_workspace_bytes(int32_t nx, int32_t ny, int32_t n_yaw);
+int seb_risk_sdf(const seb_grid* risk, float risk_obstacle, float clamp, void* work_dev, size_t work_bytes,
+                 float* sdf_dev, seb_stream_t stream);
+
+/*
  * Learned surrogate (not in the paper, which names learned traversability as less reliable
  * than geometry, Sec. II-A): a BF16 convolutional network predicting, per cell and yaw pair,
  * (z - z_cell, pitch, roll, risk) of the assessment above from an elevation patch.  Slope

@@ -9,8 +9,9 @@ state is the distance to the edge of the nearest region, negative inside obstacl
 builds it from the risk map):
 
 * Per yaw bin k, the obstacle set O_k is the cells whose risk is at least ``risk_obstacle``
-  (1 by default: the explicit obstacles of Algorithm 1, unknown cells included); the free set
-  F_k is every other cell of the window.
+  (1 by default: the explicit obstacles of Algorithm 1, unknown cells included) or NaN (an
+  unknown value counts as an obstacle, as unknown cells do in Algorithm 1); the free set F_k
+  is every other cell of the window.
 * Distances are Euclidean between cell centres in the (x, y) plane of that bin, in metres:
   ``sdf = res * (min_{o in O_k} |p - o| - min_{f in F_k} |p - f|)``.  One of the two terms is
   0, so a free cell gets its distance to the nearest obstacle and an obstacle cell minus its
@@ -51,7 +52,7 @@ def risk_sdf(risk, res, risk_obstacle=1.0, clamp=np.inf, ring=(0, 0), cells=None
     out = np.empty(len(cells))
     for k in np.unique(cells[:, 2]):
         sel = np.nonzero(cells[:, 2] == k)[0]
-        obst = R[k] >= risk_obstacle
+        obst = ~(R[k] < risk_obstacle)  # NaN: obstacle
         oy, ox = np.nonzero(obst)
         fy, fx = np.nonzero(~obst)
         py = cells[sel, 1].astype(np.float64)

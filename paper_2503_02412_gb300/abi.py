@@ -51,6 +51,8 @@ EXPORTS = (
     "seb_map_grid",
     "seb_se2_lookup",
     "seb_se2_lookup_vjp",
+    "seb_sdf_workspace_bytes",
+    "seb_risk_sdf",
     "seb_sur_workspace_bytes",
     "seb_sur_create",
     "seb_sur_destroy",
@@ -191,6 +193,8 @@ def load():
             "seb_map_grid": (ctypes.c_int, [vp, i32, ctypes.POINTER(seb_grid)]),
             "seb_se2_lookup": (ctypes.c_int, [ctypes.POINTER(seb_grid), vp, i64, ctypes.c_float, vp, vp, vp, vp]),
             "seb_se2_lookup_vjp": (ctypes.c_int, [ctypes.POINTER(seb_grid), vp, i64, vp, vp, vp]),
+            "seb_sdf_workspace_bytes": (sz, [i32, i32, i32]),
+            "seb_risk_sdf": (ctypes.c_int, [ctypes.POINTER(seb_grid), ctypes.c_float, ctypes.c_float, vp, sz, vp, vp]),
             "seb_sur_workspace_bytes": (sz, [P, i32]),
             "seb_sur_create": (ctypes.c_int, [P, i32, vp, sz, vp, ctypes.POINTER(vp)]),
             "seb_sur_destroy": (ctypes.c_int, [vp]),
@@ -315,6 +319,14 @@ def seb_se2_lookup(grid: seb_grid, poses_ptr, n, fill, val_ptr, grad_ptr=None, f
 
 def seb_se2_lookup_vjp(grid: seb_grid, poses_ptr, n, grad_val_ptr, grad_pose_ptr, stream=0) -> None:
     _check(load().seb_se2_lookup_vjp(ctypes.byref(grid), poses_ptr, n, grad_val_ptr, grad_pose_ptr, stream))
+
+
+def seb_sdf_workspace_bytes(nx, ny, n_yaw) -> int:
+    return load().seb_sdf_workspace_bytes(nx, ny, n_yaw)
+
+
+def seb_risk_sdf(risk: seb_grid, risk_obstacle, clamp, work_ptr, work_bytes, sdf_ptr, stream=0) -> None:
+    _check(load().seb_risk_sdf(ctypes.byref(risk), risk_obstacle, clamp, work_ptr, work_bytes, sdf_ptr, stream))
 
 
 def seb_query_poses_grad_noalloc(p: seb_params, elev_ptr, origin_i, origin_j, poses_ptr, n, grad_out_ptr, out_ptr,

@@ -1,0 +1,214 @@
+// Signed distance field of the obstacle set of an SE(2) risk grid (Sec. VI: the planner's
+// collision term reads an SDF over SE(2) whose value is the distance to the edge of the
+// nearest region, negative inside obstacles; the paper builds it from the risk map).
+//
+// Per yaw bin k, obstacles are the cells with risk >= risk_obstacle (NaN counts as an
+// obstacle); every other cell is free.  sdf = res * (distance to the nearest obstacle centre -
+// distance to the nearest free centre), clamped to [-clamp, clamp]: a free cell gets its
+// distance to the obstacles, an obstacle cell minus its distance to the free cells.  Distances
+// are taken in the window's logical order (the ring wrap is storage, not adjacency), and the
+// result is stored ring-indexed like the input, so the same seb_grid fields describe it.
+//
+// Exact Euclidean distances, separable: d^2(i, j) = min_j' g(i, j')^2 + (j - j')^2, with
+// g(i, j') the distance in rows to the nearest feature of column j'.  Nothing farther than
+// W = ceil(clamp / res) + 1 cells can fall under the clamp, so W bounds both passes.
+//   1. cols_kernel: sweeps every column down and up (linear time), split in 8 row segments swept
+//      by separate warps and joined through their first / last obstacle and free rows, and
+//      stores per cell the distance in rows to the nearest obstacle and to the nearest free cell
+//      of its column (uint16 each, 0xFFFF = none within W).
+//   2. rows_kernel: a block per (bin, row) stages that row's column distances in shared
+//      memory; every cell takes the minimum of g(j')^2 + (j - j')^2 over |j - j'| = 0, 1, 2, ...
+//      and stops when (j - j')^2 alone reaches the best value.  The squared distances are
+//      exact 32-bit integers.
+#include <cuda_runtime.h>
+#include <limits.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "seb.h"
+#include "seb_internal.h"
+
+namespace {
+
+constexpr uint32_t kNone = 0xFFFFu;
+constexpr int kMaxSide = 16384;
+constexpr int kSegs = 8;
+constexpr int kColThreads = 32 * kSegs;
+constexpr int kRowThreads = 256;
+constexpr int32_t kFar = 1 << 30;  // "no feature": above any W^2 (W <= 16384), kFar + W^2 < 2^31
+
+struct SdfArgs {
+  const float* risk;
+  float* sdf;
+  uint32_t* work;  // [K][ny][nx] logical: (g_obstacle << 16) | g_free
+  int nx, ny, K, ring_x, ring_y;
+  int W;           // search bound in cells (<= 16383)
+  float thr, res, clamp;
+};
+
+__device__ __forceinline__ int64_t phys(const SdfArgs& A, int k, int i, int j) {
+  int r = i + A.ring_y, c = j + A.ring_x;
+  if (r >= A.ny) r -= A.ny;
+  if (c >= A.nx) c -= A.nx;
+  return ((int64_t)k * A.ny + r) * A.nx + c;
+}
+
+__global__ void __launch_bounds__(kColThreads) cols_kernel(const SdfArgs A) {
+  // a block per (bin, 32-column stripe): lane = column, warp = one of kSegs row segments.  Each
+  // warp sweeps its segment down (distances to the nearest obstacle / free cell at or above,
+  // within the segment) and records the segment's first and last obstacle / free rows; after a
+  // barrier it sweeps up, completing each distance with the nearest rows of the other segments.
+  __shared__ int seg_rows[kSegs][4][32];  // last obstacle, first obstacle, last free, first free
+  const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane, k = blockIdx.y;
+  const int L = (A.ny + kSegs - 1) / kSegs, i0 = min(A.ny, seg * L), i1 = min(A.ny, i0 + L);
+  const bool col = j < A.nx;
+  uint32_t* out = A.work + (int64_t)k * A.ny * A.nx + j;
+  int last_o = -1, first_o = -1, last_f = -1, first_f = -1;
+  if (col) {
+#pragma unroll 4
+    for (int i = i0; i < i1; ++i) {
+      const bool ob = !(__ldg(A.risk + phys(A, k, i, j)) < A.thr);  // NaN: obstacle
+      if (ob) {
+        last_o = i;
+        first_o = first_o < 0 ? i : first_o;
+      } else {
+        last_f = i;
+        first_f = first_f < 0 ? i : first_f;
+      }
+      const uint32_t uo = last_o < 0 ? kNone : (uint32_t)(i - last_o);
+      const uint32_t uf = last_f < 0 ? kNone : (uint32_t)(i - last_f);
+      out[(int64_t)i * A.nx] = (uo << 16) | uf;
+    }
+  }
+  seg_rows[seg][0][lane] = last_o;
+  seg_rows[seg][1][lane] = first_o;
+  seg_rows[seg][2][lane] = last_f;
+  seg_rows[seg][3][lane] = first_f;
+  __syncthreads();
+  if (!col) return;
+  int above_o = -1, above_f = -1, next_o = INT_MAX, next_f = INT_MAX;
+  for (int s2 = seg - 1; s2 >= 0; --s2) {
+    if (above_o < 0) above_o = seg_rows[s2][0][lane];
+    if (above_f < 0) above_f = seg_rows[s2][2][lane];
+  }
+  for (int s2 = seg + 1; s2 < kSegs; ++s2) {
+    if (next_o == INT_MAX && seg_rows[s2][1][lane] >= 0) next_o = seg_rows[s2][1][lane];
+    if (next_f == INT_MAX && seg_rows[s2][3][lane] >= 0) next_f = seg_rows[s2][3][lane];
+  }
+  const int W = A.W;
+  auto fin = [&](uint32_t up_in_seg, int above, int next, int i) -> uint32_t {
+    int d = up_in_seg != kNone ? (int)up_in_seg : (above >= 0 ? i - above : INT_MAX);
+    if (next != INT_MAX) d = min(d, next - i);
+    return d > W ? kNone : (uint32_t)d;
+  };
+#pragma unroll 4
+  for (int i = i1 - 1; i >= i0; --i) {
+    const uint32_t v = out[(int64_t)i * A.nx];
+    const uint32_t uo = v >> 16, uf = v & 0xFFFFu;
+    if (uo == 0) next_o = i;
+    if (uf == 0) next_f = i;
+    out[(int64_t)i * A.nx] = (fin(uo, above_o, next_o, i) << 16) | fin(uf, above_f, next_f, i);
+  }
+}
+
+__global__ void __launch_bounds__(kRowThreads) rows_kernel(const SdfArgs A) {
+  extern __shared__ int32_t gsq[];  // [2][nx]: squared column distances to obstacles, to free cells
+  const int k = blockIdx.x / A.ny, i = blockIdx.x - k * A.ny;
+  const uint32_t* row = A.work + ((int64_t)k * A.ny + i) * A.nx;
+  int32_t* go2 = gsq;
+  int32_t* gf2 = gsq + A.nx;
+  for (int j = threadIdx.x; j < A.nx; j += blockDim.x) {
+    const uint32_t v = row[j];
+    const int32_t o = (int32_t)(v >> 16), f = (int32_t)(v & 0xFFFFu);
+    go2[j] = o == (int32_t)kNone ? kFar : o * o;
+    gf2[j] = f == (int32_t)kNone ? kFar : f * f;
+  }
+  __syncthreads();
+  // squared distances stay below W^2 + kFar < 2^31: 32-bit integers (64-bit ones are emulated)
+  const int32_t W2 = A.W * A.W;
+  for (int j = threadIdx.x; j < A.nx; j += blockDim.x) {
+    const bool obst = go2[j] == 0;
+    const int32_t* h = obst ? gf2 : go2;  // obstacle cells search the free cells, and the reverse
+    int32_t best = h[j];
+    const int lim = min(A.W, max(j, A.nx - 1 - j)), last = A.nx - 1;
+    // Offsets past a row end re-read the end column at an overstated distance (its true offset
+    // was already counted), which cannot lower the minimum: the indices are clamped instead of
+    // tested.  Two offsets per step; the early exit is checked before each pair.
+    for (int s = 1; s <= lim; s += 2) {
+      const int32_t s2 = s * s;
+      if (s2 >= best) break;  // every farther column is at least s^2 away
+      const int32_t t2 = s2 + 2 * s + 1;
+      const int32_t a0 = h[max(j - s, 0)], b0 = h[min(j + s, last)];
+      const int32_t a1 = h[max(j - s - 1, 0)], b1 = h[min(j + s + 1, last)];
+      best = min(best, min(s2 + min(a0, b0), t2 + min(a1, b1)));
+    }
+    float d = best > W2 ? INFINITY : A.res * sqrtf((float)best);
+    d = fminf(d, A.clamp);
+    A.sdf[phys(A, k, i, j)] = obst ? -d : d;
+  }
+}
+
+}  // namespace
+
+extern "C" size_t seb_sdf_workspace_bytes(int32_t nx, int32_t ny, int32_t n_yaw) {
+  if (nx < 1 || ny < 1 || n_yaw < 1 || nx > kMaxSide || ny > kMaxSide) return 0;
+  return (size_t)nx * ny * n_yaw * sizeof(uint32_t);
+}
+
+extern "C" int seb_risk_sdf(const seb_grid* g, float risk_obstacle, float clamp, void* work, size_t work_bytes,
+                            float* sdf, seb_stream_t stream) {
+  if (!g || !g->data || !sdf || !work) {
+    seb::set_error("seb_risk_sdf: NULL grid, output or workspace");
+    return SEB_ERR_INVALID_ARG;
+  }
+  if (g->nx < 1 || g->ny < 1 || g->n_yaw < 1 || g->nx > kMaxSide || g->ny > kMaxSide || g->ring_x < 0 ||
+      g->ring_x >= g->nx || g->ring_y < 0 || g->ring_y >= g->ny || !(g->res > 0.f)) {
+    seb::set_error("seb_risk_sdf: bad grid shape (1 <= nx, ny <= %d, n_yaw >= 1, 0 <= ring < n, res > 0)",
+                   kMaxSide);
+    return SEB_ERR_BAD_SHAPE;
+  }
+  if (!(clamp >= 0.f)) {
+    seb::set_error("seb_risk_sdf: clamp must be >= 0 (inf for none)");
+    return SEB_ERR_INVALID_ARG;
+  }
+  const size_t need = seb_sdf_workspace_bytes(g->nx, g->ny, g->n_yaw);
+  if (work_bytes < need || ((uintptr_t)work & 3)) {
+    seb::set_error("seb_risk_sdf: workspace too small or misaligned (%zu bytes needed)", need);
+    return SEB_ERR_WORKSPACE;
+  }
+  if ((const void*)sdf == (const void*)g->data) {
+    seb::set_error("seb_risk_sdf: the output may not alias the risk grid");
+    return SEB_ERR_INVALID_ARG;
+  }
+  SdfArgs A;
+  A.risk = g->data;
+  A.sdf = sdf;
+  A.work = static_cast<uint32_t*>(work);
+  A.nx = g->nx;
+  A.ny = g->ny;
+  A.K = g->n_yaw;
+  A.ring_x = g->ring_x;
+  A.ring_y = g->ring_y;
+  A.thr = risk_obstacle;
+  A.res = g->res;
+  A.clamp = clamp;
+  // search bound: the diagonal always suffices; a finite clamp caps it at clamp / res + 1
+  const double side = (double)(g->nx > g->ny ? g->nx : g->ny);
+  double w = ceil((double)clamp / (double)g->res) + 1.0;
+  if (!(w < side)) w = side;
+  A.W = (int)w;
+  const cudaStream_t st = (cudaStream_t)stream;
+  cols_kernel<<<dim3((unsigned)((A.nx + 31) / 32), (unsigned)A.K), kColThreads, 0, st>>>(A);
+  cudaError_t e = cudaFuncSetAttribute(rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(2 * A.nx * sizeof(int32_t)));
+  if (e == cudaSuccess) {
+    rows_kernel<<<(unsigned)((int64_t)A.K * A.ny), kRowThreads, 2 * A.nx * sizeof(int32_t), st>>>(A);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    seb::set_error("seb_risk_sdf launch: %s", cudaGetErrorString(e));
+    return SEB_ERR_CUDA;
+  }
+  return SEB_OK;
+}

@@ -5,8 +5,10 @@ on SO(2)).
 ``SE2Grid`` names one ring-indexed [n_yaw][ny][nx] float32 channel on the device: a channel of
 a ``SebMap`` (``SE2Grid.from_map``) or any caller tensor (``SE2Grid.from_tensor``).
 ``se2_lookup`` returns values, optional world-unit gradients and flags; ``SE2Lookup`` is the
-differentiable form whose backward runs the adjoint kernel.  Both kernels are libseb's
-(``seb_se2_lookup`` / ``seb_se2_lookup_vjp``); this module only marshals tensors.
+differentiable form whose backward runs the adjoint kernel; ``risk_sdf`` builds the signed
+distance field of the obstacle set as another grid.  The kernels are libseb's
+(``seb_se2_lookup``, ``seb_se2_lookup_vjp``, ``seb_risk_sdf``); this module only marshals
+tensors.
 """
 from __future__ import annotations
 
@@ -61,6 +63,25 @@ def se2_lookup(grid: SE2Grid, poses: torch.Tensor, fill: float = math.nan, with_
     abi.seb_se2_lookup(grid.g, poses.data_ptr(), n, float(fill), val.data_ptr(),
                        grad.data_ptr() if grad is not None else None, flags.data_ptr(), _stream(poses))
     return val, grad, flags
+
+
+def risk_sdf(risk: SE2Grid, risk_obstacle: float = 1.0, clamp: float = math.inf, out: torch.Tensor = None,
+             work: torch.Tensor = None) -> SE2Grid:
+    """Signed distance field (metres) of the obstacle set (risk >= risk_obstacle) of every yaw
+    bin of a risk grid, stored ring-indexed like it; returns it as an SE2Grid for lookups."""
+    g = risk.g
+    shape = (g.n_yaw, g.ny, g.nx)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=risk.device)
+    if tuple(out.shape) != shape or out.dtype != torch.float32 or not out.is_contiguous():
+        raise ValueError(f"out must be a contiguous float32 tensor of shape {shape}")
+    nb = abi.seb_sdf_workspace_bytes(g.nx, g.ny, g.n_yaw)
+    if work is None or work.numel() * work.element_size() < nb:
+        work = torch.empty(nb, dtype=torch.uint8, device=risk.device)
+    abi.seb_risk_sdf(g, float(risk_obstacle), float(clamp), work.data_ptr(), nb, out.data_ptr(),
+                     _stream(out))
+    sg = abi.seb_grid(out.data_ptr(), g.nx, g.ny, g.n_yaw, g.ring_x, g.ring_y, g.origin_i, g.origin_j, g.res)
+    return SE2Grid(sg, out, risk.device)
 
 
 class SE2Lookup(torch.autograd.Function):

@@ -9,6 +9,7 @@ from .terrain import (  # noqa: F401
     fractal_steps_nan,
     fractal_world,
     lookup_poses,
+    obstacle_risk,
     random_se2_grid,
     shift_sequence,
     random_poses,

@@ -156,3 +156,19 @@ def lookup_poses(seed, n, nx, ny, res, origin=(0, 0), pad_cells=2.0, yaw_range=2
     y = (oj + 0.5 + rng.uniform(-pad_cells, ny - 1 + pad_cells, size=n)) * res
     th = rng.uniform(-yaw_range, yaw_range, size=n)
     return np.stack([x, y, th], axis=1).astype(dtype)
+
+
+def obstacle_risk(seed, n_yaw, ny, nx, n_blobs=12, blob_cells=(2, 12), nan_frac=0.0, dtype=np.float32):
+    """A [n_yaw][ny][nx] risk grid: U[0, 0.9) everywhere, and risk 1 inside n_blobs discs per
+    yaw bin (radius U[blob_cells] cells, centres uniform), plus an optional NaN fraction."""
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(0.0, 0.9, size=(n_yaw, ny, nx))
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    for k in range(n_yaw):
+        for _ in range(n_blobs):
+            cy, cx = rng.uniform(0, ny), rng.uniform(0, nx)
+            rad = rng.uniform(*blob_cells)
+            r[k][(yy - cy) ** 2 + (xx - cx) ** 2 <= rad * rad] = 1.0
+    if nan_frac > 0:
+        r[rng.random(r.shape) < nan_frac] = np.nan
+    return r.astype(dtype)

@@ -43,6 +43,16 @@ def test_half_plane_is_linear_and_clamped():
     assert np.allclose(sdf, np.clip(ref, -0.35, 0.35)[None, None, :], atol=1e-12)
 
 
+def test_nan_is_an_obstacle():
+    risk = np.zeros((1, 9, 9))
+    risk[0, 4, 4] = np.nan
+    sdf = risk_sdf(risk, RES)
+    r, c = np.mgrid[0:9, 0:9]
+    ref = RES * np.hypot(r - 4, c - 4)
+    ref[4, 4] = -RES
+    assert np.allclose(sdf[0], ref, atol=1e-12)
+
+
 def test_empty_and_full_sets_and_threshold():
     risk = np.full((2, 5, 6), 0.5)
     risk[1] = 1.0
