@@ -439,7 +439,16 @@ def measure_rows(seb, args, dev):
                               "lookup_1M_value_grad_ms": tl2,
                               "hbm_gbs": 16 * NX * NY * K / ts / 1e6,  # risk in, work out + in, sdf out
                               "config": "risk channel of the 400x400x72 fractal map, obstacles risk >= 1, clamp 2 m"}
-    del mc2, sdf_t, work, p2, v2, g2, sdf_grid, risk
+    # nearest-neighbour inpainting of the same map before its assessment
+    e2 = torch.from_numpy(fractal_steps_nan(0)).to(dev)
+    filled = torch.empty_like(e2)
+    iw = torch.empty(abi.seb_inpaint_workspace_bytes(NX, NY), dtype=torch.uint8, device=dev)
+    ti = _time(lambda: seb.inpaint_nearest(e2, 0, out=filled, work=iw), 20, st)
+    tu = _time(lambda: mc2.update(filled), 10, st)
+    n_unknown_raw = float(torch.isnan(e2).float().mean())
+    rows["inpaint_400x400"] = {"inpaint_ms": ti, "rebuild_after_inpaint_ms": tu, "unknown_frac_before": n_unknown_raw,
+                               "config": "fractal map with 5 % NaN discs, unbounded nearest-neighbour filling"}
+    del mc2, sdf_t, work, p2, v2, g2, sdf_grid, risk, e2, filled, iw
     # S8
     e3 = torch.from_numpy(bumpy_plane(21, 1024, 1024, 0.05)).to(dev)
     prec = {}

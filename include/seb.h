@@ -268,6 +268,21 @@ int seb_risk_sdf(const seb_grid* risk, float risk_obstacle, float clamp, void* w
                  float* sdf_dev, seb_stream_t stream);
 
 /*
+ * Nearest-neighbour inpainting of an elevation map (Sec. V-A: the map is inpainted before the
+ * traversability pass; Sec. VII-B: nearest-neighbour filling).  elev_dev [ny][nx] float32 in
+ * logical order, NaN = unknown.  Every unknown cell of out_dev [ny][nx] takes the value of the
+ * known cell whose centre is nearest (Euclidean); among equally near known cells the smallest
+ * column, then the smallest row wins; known cells are copied.  max_cells > 0 leaves unknown
+ * the cells whose nearest known cell is farther than max_cells cells; a map without known
+ * cells stays unknown.  source_dev [ny][nx][2] int32 (may be NULL) receives the (row, column)
+ * each value came from, (-1, -1) where none.  out_dev may not alias elev_dev.  work_dev:
+ * caller-owned, 4-byte aligned, seb_inpaint_workspace_bytes(nx, ny) bytes.  Sides up to 16384.
+ */
+size_t seb_inpaint_workspace_bytes(int32_t nx, int32_t ny);
+int seb_inpaint_nearest(const float* elev_dev, int32_t nx, int32_t ny, int32_t max_cells, void* work_dev,
+                        size_t work_bytes, float* out_dev, int32_t* source_dev, seb_stream_t stream);
+
+/*
  * Learned surrogate (not in the paper, which names learned traversability as less reliable
  * than geometry, Sec. II-A): a BF16 convolutional network predicting, per cell and yaw pair,
  * (z - z_cell, pitch, roll, risk) of the assessment above from an elevation patch.  Slope

@@ -39,14 +39,15 @@ def inpaint_nearest(elev, max_cells=0):
     # candidates sorted by (col, row) so that the first minimum is the tie-break winner
     order = np.lexsort((kr, kc))
     kr, kc = kr[order], kc[order]
-    for s in range(0, len(ur), 2048):
-        r = ur[s:s + 2048, None]
-        c = uc[s:s + 2048, None]
+    step = max(1, (1 << 23) // len(kr))  # rows of the pair matrix per chunk (~64 MB)
+    for s in range(0, len(ur), step):
+        r = ur[s:s + step, None]
+        c = uc[s:s + step, None]
         d2 = (r - kr[None, :]) ** 2 + (c - kc[None, :]) ** 2
         best = np.argmin(d2, axis=1)  # first occurrence: smallest (col, row) among the nearest
         bd2 = d2[np.arange(len(best)), best]
         ok = np.ones(len(best), bool) if max_cells <= 0 else bd2 <= max_cells * max_cells
-        rr, cc = ur[s:s + 2048][ok], uc[s:s + 2048][ok]
+        rr, cc = ur[s:s + step][ok], uc[s:s + step][ok]
         out[rr, cc] = z[kr[best[ok]], kc[best[ok]]]
         src[rr, cc, 0] = kr[best[ok]]
         src[rr, cc, 1] = kc[best[ok]]

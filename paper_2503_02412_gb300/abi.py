@@ -53,6 +53,8 @@ EXPORTS = (
     "seb_se2_lookup_vjp",
     "seb_sdf_workspace_bytes",
     "seb_risk_sdf",
+    "seb_inpaint_workspace_bytes",
+    "seb_inpaint_nearest",
     "seb_sur_workspace_bytes",
     "seb_sur_create",
     "seb_sur_destroy",
@@ -195,6 +197,8 @@ def load():
             "seb_se2_lookup_vjp": (ctypes.c_int, [ctypes.POINTER(seb_grid), vp, i64, vp, vp, vp]),
             "seb_sdf_workspace_bytes": (sz, [i32, i32, i32]),
             "seb_risk_sdf": (ctypes.c_int, [ctypes.POINTER(seb_grid), ctypes.c_float, ctypes.c_float, vp, sz, vp, vp]),
+            "seb_inpaint_workspace_bytes": (sz, [i32, i32]),
+            "seb_inpaint_nearest": (ctypes.c_int, [vp, i32, i32, i32, vp, sz, vp, vp, vp]),
             "seb_sur_workspace_bytes": (sz, [P, i32]),
             "seb_sur_create": (ctypes.c_int, [P, i32, vp, sz, vp, ctypes.POINTER(vp)]),
             "seb_sur_destroy": (ctypes.c_int, [vp]),
@@ -327,6 +331,14 @@ def seb_sdf_workspace_bytes(nx, ny, n_yaw) -> int:
 
 def seb_risk_sdf(risk: seb_grid, risk_obstacle, clamp, work_ptr, work_bytes, sdf_ptr, stream=0) -> None:
     _check(load().seb_risk_sdf(ctypes.byref(risk), risk_obstacle, clamp, work_ptr, work_bytes, sdf_ptr, stream))
+
+
+def seb_inpaint_workspace_bytes(nx, ny) -> int:
+    return load().seb_inpaint_workspace_bytes(nx, ny)
+
+
+def seb_inpaint_nearest(elev_ptr, nx, ny, max_cells, work_ptr, work_bytes, out_ptr, source_ptr=None, stream=0) -> None:
+    _check(load().seb_inpaint_nearest(elev_ptr, nx, ny, max_cells, work_ptr, work_bytes, out_ptr, source_ptr, stream))
 
 
 def seb_query_poses_grad_noalloc(p: seb_params, elev_ptr, origin_i, origin_j, poses_ptr, n, grad_out_ptr, out_ptr,
