@@ -8,6 +8,7 @@ from .terrain import (  # noqa: F401
     bumpy_plane,
     fractal_steps_nan,
     fractal_world,
+    lidar_scan,
     lookup_poses,
     obstacle_risk,
     random_se2_grid,

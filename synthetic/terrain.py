@@ -172,3 +172,52 @@ def obstacle_risk(seed, n_yaw, ny, nx, n_blobs=12, blob_cells=(2, 12), nan_frac=
     if nan_frac > 0:
         r[rng.random(r.shape) < nan_frac] = np.nan
     return r.astype(dtype)
+
+
+def _rot_zyx(yaw, pitch, roll):
+    cy, sy, cp, sp, cr, sr = np.cos(yaw), np.sin(yaw), np.cos(pitch), np.sin(pitch), np.cos(roll), np.sin(roll)
+    Rz = np.array([[cy, -sy, 0], [sy, cy, 0], [0, 0, 1.0]])
+    Ry = np.array([[cp, 0, sp], [0, 1.0, 0], [-sp, 0, cp]])
+    Rx = np.array([[1.0, 0, 0], [0, cr, -sr], [0, sr, cr]])
+    return Rz @ Ry @ Rx
+
+
+def lidar_scan(seed, world, res, x, y, yaw=0.0, n_rings=32, n_az=1024, fov_deg=(-15.0, 15.0), max_range=12.0,
+               body_height=0.45, p_BS=(0.1, 0.0, 0.25), tilt_deg=2.0, range_noise=0.01):
+    """A synthetic spinning-LiDAR scan of a world heightfield [ny][nx] (world cell (i, j) centred
+    at ((i + 1/2) res, (j + 1/2) res); NaN cells are not hit).
+
+    The body sits body_height above the terrain at (x, y) with heading yaw and a random tilt of
+    up to tilt_deg; the sensor, at p_BS in the body frame with the body's attitude, casts
+    n_rings x n_az rays (elevations uniform over fov_deg, azimuths uniform) and each ray stops at
+    the first sample, every res / 2, below the terrain (nearest cell), plus N(0, range_noise)
+    range noise.  Returns (R_B, p_B, R_BS, p_BS, points [m][3] in the sensor frame, float32)."""
+    rng = np.random.default_rng(seed)
+    z = np.asarray(world, np.float64)
+    ny, nx = z.shape
+
+    def height(px, py):
+        i = np.clip(np.floor(px / res).astype(np.int64), 0, nx - 1)
+        j = np.clip(np.floor(py / res).astype(np.int64), 0, ny - 1)
+        return z[j, i]
+
+    g = height(np.array([x]), np.array([y]))[0]
+    g = 0.0 if np.isnan(g) else g
+    R_B = _rot_zyx(yaw, *np.deg2rad(rng.uniform(-tilt_deg, tilt_deg, 2)))
+    p_B = np.array([x, y, g + body_height])
+    R_BS = np.eye(3)
+    p_BS = np.asarray(p_BS, np.float64)
+    origin = R_B @ p_BS + p_B
+    el = np.deg2rad(np.linspace(fov_deg[0], fov_deg[1], n_rings))
+    az = np.linspace(0, 2 * np.pi, n_az, endpoint=False)
+    E, A = np.meshgrid(el, az, indexing="ij")
+    d_s = np.stack([np.cos(E) * np.cos(A), np.cos(E) * np.sin(A), np.sin(E)], -1).reshape(-1, 3)
+    d_w = d_s @ (R_B @ R_BS).T
+    steps = np.arange(1, int(max_range / (res / 2)) + 1) * (res / 2)
+    pts = origin[None, None, :] + steps[None, :, None] * d_w[:, None, :]
+    below = pts[..., 2] <= height(pts[..., 0], pts[..., 1])
+    hit = below.any(axis=1)
+    first = np.argmax(below, axis=1)
+    r = steps[first[hit]] + rng.normal(0.0, range_noise, hit.sum())
+    sensor_pts = d_s[hit] * r[:, None]
+    return R_B, p_B, R_BS, p_BS, sensor_pts.astype(np.float32)
