@@ -283,6 +283,65 @@ int seb_inpaint_nearest(const float* elev_dev, int32_t nx, int32_t ny, int32_t m
                         size_t work_bytes, float* out_dev, int32_t* source_dev, seb_stream_t stream);
 
 /*
+ * Elevation-map update from LiDAR scans (Sec. V-A).  The map is a robot-centred window of
+ * nx x ny cells at res metres, each holding a height and its variance (NaN = unknown), stored
+ * at [world row mod ny][world column mod nx].  seb_elev_integrate takes one scan and, in the
+ * order of Sec. V-A:
+ *  1. sets the window origin to the robot's cell minus (nx / 2, ny / 2) (Eq. pm) and clears
+ *     the cells that were not in the previous window;
+ *  2. ray casting: for every point whose (x, y) lies in the window, clears each cell that the
+ *     segment sensor -> point crosses in (x, y), the point's own cell excepted, when the cell's
+ *     height exceeds the ray's highest height over it plus clear_margin;
+ *  3. ignores points outside the window and keeps those whose body-frame height lies in
+ *     [z_min, z_max]; a kept point has world height z = b3^T (R_B (R_BS p + p_BS) + p_B) and
+ *     variance J_S^T Sigma_S J_S + J_R^T Sigma_R J_R + J_B^T Sigma_B J_B, J_S = (R_B R_BS)^T b3,
+ *     J_R = (R_BS p + p_BS)^ R_B^T b3 (right perturbation of R_B), J_B = -b3;
+ *  4. fuses the kept points per cell (one-dimensional Kalman filter, information form) against
+ *     the estimate (h, s2) from before this fusion: a point with (z - h) / sqrt(s2) > gate is
+ *     above the gate, one within [-gate, gate] inside, one below is dropped; a cell with points
+ *     above the gate is reset to their fusion, otherwise its estimate is fused with the points
+ *     inside; an unknown cell takes the fusion of all its points.
+ * The result does not depend on the order of the points.  Matrices are row-major float32;
+ * points_dev [n][3] float32 in the sensor frame, n <= max_points.  The workspace is
+ * caller-owned, 256-byte aligned device memory of seb_elev_workspace_bytes() bytes.
+ */
+typedef struct {
+  int32_t nx, ny;
+  float res;
+  float z_min, z_max;   /* body-frame height filter (m) */
+  float gate;           /* Mahalanobis gate (standard deviations), default 2.5 */
+  float clear_margin;   /* ray casting clears cells higher than the ray by more than this (m) */
+} seb_elev_params;
+
+typedef struct {
+  float R_B[9], p_B[3];     /* body -> world rotation and body position */
+  float R_BS[9], p_BS[3];   /* sensor -> body rotation and sensor position in the body frame */
+  float Sigma_S[9];         /* point covariance (sensor model) */
+  float Sigma_R[9];         /* attitude covariance */
+  float Sigma_B[9];         /* position covariance */
+} seb_scan_pose;
+
+typedef struct {
+  float* height;            /* [ny][nx], storage order (see above) */
+  float* variance;
+  int32_t ring_x, ring_y;   /* storage column = (logical column + ring_x) mod nx, same for rows */
+  int64_t origin_i, origin_j;
+} seb_elev_view;
+
+typedef struct seb_elev seb_elev;
+
+void seb_elev_params_default(seb_elev_params* p);
+size_t seb_elev_workspace_bytes(const seb_elev_params* p, int64_t max_points);
+int seb_elev_create(const seb_elev_params* p, int64_t max_points, void* workspace_dev, size_t bytes,
+                    seb_stream_t stream, seb_elev** out);
+int seb_elev_destroy(seb_elev* e);
+int seb_elev_set_stream(seb_elev* e, seb_stream_t stream);
+int seb_elev_integrate(seb_elev* e, const seb_scan_pose* pose, const float* points_dev, int64_t n);
+int seb_elev_view_get(const seb_elev* e, seb_elev_view* v);
+/* Heights / variances in logical (window) order [ny][nx]; either pointer may be NULL. */
+int seb_elev_copy_out(const seb_elev* e, float* height_dev, float* variance_dev);
+
+/*
  * Learned surrogate (not in the paper, which names learned traversability as less reliable
  * than geometry, Sec. II-A): a BF16 convolutional network predicting, per cell and yaw pair,
  * (z - z_cell, pitch, roll, risk) of the assessment above from an elevation patch.  Slope

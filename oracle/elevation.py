@@ -87,8 +87,12 @@ def point_heights(pose: ScanPose, pts):
 
 
 class ElevationMap:
-    def __init__(self, p: ElevParams):
+    """store_f32: round the stored heights and variances to float32 after every scan, so that
+    the next scan's gate and clearing decisions are taken on the values a float32 map holds."""
+
+    def __init__(self, p: ElevParams, store_f32=False):
         self.p = p
+        self.store_f32 = store_f32
         self.h = np.full((p.ny, p.nx), np.nan)   # storage: [world j mod ny][world i mod nx]
         self.s2 = np.full((p.ny, p.nx), np.nan)
         self.origin = None
@@ -128,7 +132,16 @@ class ElevationMap:
             j0, j1 = int(np.floor(min(sy, y) / res)), int(np.floor(max(sy, y) / res))
             pi, pj = int(np.floor(x / res)), int(np.floor(y / res))
             for wi in range(i0, i1 + 1):
-                for wj in range(j0, j1 + 1):
+                # candidate rows of this column: the segment's y-range over the column's x-range,
+                # widened by one cell (the slab test below decides every candidate)
+                if dx != 0.0:
+                    ta, tb = sorted(((wi * res - sx) / dx, ((wi + 1) * res - sx) / dx))
+                    ta, tb = max(ta, 0.0), min(tb, 1.0)
+                    ya, yb = sorted((sy + dy * ta, sy + dy * tb))
+                    jlo, jhi = max(j0, int(np.floor(ya / res)) - 1), min(j1, int(np.floor(yb / res)) + 1)
+                else:
+                    jlo, jhi = j0, j1
+                for wj in range(jlo, jhi + 1):
                     if (wi, wj) == (pi, pj):
                         continue
                     c, r = wi - self.origin[0], wj - self.origin[1]
@@ -195,4 +208,7 @@ class ElevationMap:
                     W, WZ = a[0] + 1.0 / v0[pr, pc], a[1] + h0[pr, pc] / v0[pr, pc]
                 self.s2[pr, pc] = 1.0 / W
                 self.h[pr, pc] = WZ / W
+        if self.store_f32:
+            self.h = self.h.astype(np.float32).astype(np.float64)
+            self.s2 = self.s2.astype(np.float32).astype(np.float64)
         return o

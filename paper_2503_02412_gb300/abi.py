@@ -55,6 +55,14 @@ EXPORTS = (
     "seb_risk_sdf",
     "seb_inpaint_workspace_bytes",
     "seb_inpaint_nearest",
+    "seb_elev_params_default",
+    "seb_elev_workspace_bytes",
+    "seb_elev_create",
+    "seb_elev_destroy",
+    "seb_elev_set_stream",
+    "seb_elev_integrate",
+    "seb_elev_view_get",
+    "seb_elev_copy_out",
     "seb_sur_workspace_bytes",
     "seb_sur_create",
     "seb_sur_destroy",
@@ -109,6 +117,23 @@ class seb_grid(ctypes.Structure):
         ("origin_j", ctypes.c_int64),
         ("res", ctypes.c_float),
     ]
+
+
+class seb_elev_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("res", ctypes.c_float),
+                ("z_min", ctypes.c_float), ("z_max", ctypes.c_float), ("gate", ctypes.c_float),
+                ("clear_margin", ctypes.c_float)]
+
+
+class seb_scan_pose(ctypes.Structure):
+    _fields_ = [("R_B", ctypes.c_float * 9), ("p_B", ctypes.c_float * 3), ("R_BS", ctypes.c_float * 9),
+                ("p_BS", ctypes.c_float * 3), ("Sigma_S", ctypes.c_float * 9), ("Sigma_R", ctypes.c_float * 9),
+                ("Sigma_B", ctypes.c_float * 9)]
+
+
+class seb_elev_view(ctypes.Structure):
+    _fields_ = [("height", ctypes.c_void_p), ("variance", ctypes.c_void_p), ("ring_x", ctypes.c_int32),
+                ("ring_y", ctypes.c_int32), ("origin_i", ctypes.c_int64), ("origin_j", ctypes.c_int64)]
 
 
 class seb_view(ctypes.Structure):
@@ -199,6 +224,14 @@ def load():
             "seb_risk_sdf": (ctypes.c_int, [ctypes.POINTER(seb_grid), ctypes.c_float, ctypes.c_float, vp, sz, vp, vp]),
             "seb_inpaint_workspace_bytes": (sz, [i32, i32]),
             "seb_inpaint_nearest": (ctypes.c_int, [vp, i32, i32, i32, vp, sz, vp, vp, vp]),
+            "seb_elev_params_default": (None, [ctypes.POINTER(seb_elev_params)]),
+            "seb_elev_workspace_bytes": (sz, [ctypes.POINTER(seb_elev_params), i64]),
+            "seb_elev_create": (ctypes.c_int, [ctypes.POINTER(seb_elev_params), i64, vp, sz, vp, ctypes.POINTER(vp)]),
+            "seb_elev_destroy": (ctypes.c_int, [vp]),
+            "seb_elev_set_stream": (ctypes.c_int, [vp, vp]),
+            "seb_elev_integrate": (ctypes.c_int, [vp, ctypes.POINTER(seb_scan_pose), vp, i64]),
+            "seb_elev_view_get": (ctypes.c_int, [vp, ctypes.POINTER(seb_elev_view)]),
+            "seb_elev_copy_out": (ctypes.c_int, [vp, vp, vp]),
             "seb_sur_workspace_bytes": (sz, [P, i32]),
             "seb_sur_create": (ctypes.c_int, [P, i32, vp, sz, vp, ctypes.POINTER(vp)]),
             "seb_sur_destroy": (ctypes.c_int, [vp]),
@@ -339,6 +372,44 @@ def seb_inpaint_workspace_bytes(nx, ny) -> int:
 
 def seb_inpaint_nearest(elev_ptr, nx, ny, max_cells, work_ptr, work_bytes, out_ptr, source_ptr=None, stream=0) -> None:
     _check(load().seb_inpaint_nearest(elev_ptr, nx, ny, max_cells, work_ptr, work_bytes, out_ptr, source_ptr, stream))
+
+
+def seb_elev_params_default() -> seb_elev_params:
+    p = seb_elev_params()
+    load().seb_elev_params_default(ctypes.byref(p))
+    return p
+
+
+def seb_elev_workspace_bytes(p: seb_elev_params, max_points) -> int:
+    return load().seb_elev_workspace_bytes(ctypes.byref(p), max_points)
+
+
+def seb_elev_create(p: seb_elev_params, max_points, ws_ptr, nbytes, stream=0):
+    h = ctypes.c_void_p()
+    _check(load().seb_elev_create(ctypes.byref(p), max_points, ws_ptr, nbytes, stream, ctypes.byref(h)))
+    return h.value
+
+
+def seb_elev_destroy(h) -> None:
+    load().seb_elev_destroy(h)
+
+
+def seb_elev_set_stream(h, stream) -> None:
+    _check(load().seb_elev_set_stream(h, stream))
+
+
+def seb_elev_integrate(h, pose: seb_scan_pose, points_ptr, n) -> None:
+    _check(load().seb_elev_integrate(h, ctypes.byref(pose), points_ptr, n))
+
+
+def seb_elev_view_get(h) -> seb_elev_view:
+    v = seb_elev_view()
+    _check(load().seb_elev_view_get(h, ctypes.byref(v)))
+    return v
+
+
+def seb_elev_copy_out(h, height_ptr, variance_ptr) -> None:
+    _check(load().seb_elev_copy_out(h, height_ptr, variance_ptr))
 
 
 def seb_query_poses_grad_noalloc(p: seb_params, elev_ptr, origin_i, origin_j, poses_ptr, n, grad_out_ptr, out_ptr,
