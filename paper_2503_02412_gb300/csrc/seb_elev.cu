@@ -14,8 +14,8 @@
 //
 // Kernels, per scan: move (clear the cells that entered the window), points (FP64 transform,
 // filters, cell, variance: a scan has ~1e4-1e5 points, so FP64 costs little and the cell index
-// and the gate decision match an FP64 evaluation), raycast (one thread per point, FP64
-// Amanatides-Woo walk; clearing is idempotent, so rays may race), accumulate (FP64 atomics of
+// and the gate decision match an FP64 evaluation), raycast (FP64 Amanatides-Woo walks, 8
+// segments per ray; clearing is idempotent, so walks may race), accumulate (FP64 atomics of
 // the information sums per cell) and finalize (one thread per cell).
 #include <cuda_runtime.h>
 #include <math.h>
@@ -39,6 +39,7 @@ struct seb_elev {
   double* pz;     // [max_points][2]: world height, variance
   uint8_t* inside;// [max_points]: (x, y) inside the window (ray casting)
   double* pw;     // [max_points][3]: world point
+  double* rinv;   // [max_points][2]: 1 / dx, 1 / dy of the ray sensor -> point, in cells
   int64_t oi, oj;
   bool valid;
 };
@@ -93,7 +94,8 @@ __global__ void move_kernel(ElevArgs A, float* h, float* s2) {
 }
 
 __global__ void points_kernel(ElevArgs A, const float* __restrict__ pts, int64_t n, int32_t* __restrict__ cell,
-                              double* __restrict__ pz, uint8_t* __restrict__ inside, double* __restrict__ pw) {
+                              double* __restrict__ pz, uint8_t* __restrict__ inside, double* __restrict__ pw,
+                              double* __restrict__ rinv) {
   double JS[3], RtB[3];
   {
     // J_S = (R_B R_BS)^T b3: the third row of R_B R_BS; R_B^T b3: the third row of R_B
@@ -118,6 +120,10 @@ __global__ void points_kernel(ElevArgs A, const float* __restrict__ pts, int64_t
     const bool in = fin && fi >= (double)A.oi && fi < (double)(A.oi + A.nx) && fj >= (double)A.oj &&
                     fj < (double)(A.oj + A.ny);
     inside[i] = in;
+    // reciprocals of the ray's extent in cells (0 for an axis it does not move along)
+    const double dxc = w[0] * A.inv_res - A.sx * A.inv_res, dyc = w[1] * A.inv_res - A.sy * A.inv_res;
+    rinv[2 * i] = dxc != 0.0 ? 1.0 / dxc : 0.0;
+    rinv[2 * i + 1] = dyc != 0.0 ? 1.0 / dyc : 0.0;
     const bool keep = in && b[2] >= A.z_min && b[2] <= A.z_max;
     cell[i] = keep ? (int32_t)store_idx(A, (int64_t)fi, (int64_t)fj) : -1;
     if (keep) {
@@ -131,42 +137,79 @@ __global__ void points_kernel(ElevArgs A, const float* __restrict__ pts, int64_t
 
 // Walk of the cells crossed by the segment sensor -> point in (x, y) (Amanatides & Woo), in
 // world cell units; clears a crossed cell (the point's own excepted) whose height exceeds the
-// ray's highest height over it plus the margin.
-__global__ void raycast_kernel(ElevArgs A, const double* __restrict__ pw, const uint8_t* __restrict__ inside,
-                               int64_t n, float* h, float* s2) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+// ray's highest height over it plus the margin.  Each ray's parameter range [0, 1] is split in
+// kRaySegs segments walked by separate threads (a scan has only ~1e4 rays): a segment starts at
+// the cell holding its start point, with that cell's full entry / exit interval, and stops once
+// the next cell is entered at or after its end.  A cell at a segment boundary may be tested by
+// both neighbours, never by neither; clearing is idempotent, so that is harmless, and so are
+// races between rays.  Four cells per round: indices and ray tops first, then their height loads
+// together, then the tests.
+constexpr int kRaySegs = 8;
+
+__global__ void raycast_kernel(ElevArgs A, const double* __restrict__ pw, const double* __restrict__ rinv,
+                               const uint8_t* __restrict__ inside, int64_t n, float* h, float* s2) {
+  const double sx = A.sx * A.inv_res, sy = A.sy * A.inv_res, sz = A.sz;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * kRaySegs;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / kRaySegs;
+    const int seg = (int)(t - i * kRaySegs);
     if (!inside[i]) continue;
     const double ex = pw[3 * i] * A.inv_res, ey = pw[3 * i + 1] * A.inv_res, ez = pw[3 * i + 2];
-    const double sx = A.sx * A.inv_res, sy = A.sy * A.inv_res, sz = A.sz;
     const double dx = ex - sx, dy = ey - sy, dz = ez - sz;
-    int64_t ci = (int64_t)floor(sx), cj = (int64_t)floor(sy);
-    const int64_t ei = (int64_t)floor(ex), ej = (int64_t)floor(ey);
+    const double ix = rinv[2 * i], iy = rinv[2 * i + 1];  // 1 / dx, 1 / dy (0 when that extent is 0)
     const int stx = dx > 0 ? 1 : (dx < 0 ? -1 : 0), sty = dy > 0 ? 1 : (dy < 0 ? -1 : 0);
-    const double tdx = stx ? 1.0 / fabs(dx) : INFINITY, tdy = sty ? 1.0 / fabs(dy) : INFINITY;
-    double tmx = stx > 0 ? (ci + 1 - sx) / dx : (stx < 0 ? (ci - sx) / dx : INFINITY);
-    double tmy = sty > 0 ? (cj + 1 - sy) / dy : (sty < 0 ? (cj - sy) / dy : INFINITY);
-    double t0 = 0.0;
+    const int64_t ei = (int64_t)floor(ex), ej = (int64_t)floor(ey);
+    const double ts = (double)seg / kRaySegs, te = (double)(seg + 1) / kRaySegs;
+    int64_t ci = (int64_t)floor(seg == 0 ? sx : sx + dx * ts), cj = (int64_t)floor(seg == 0 ? sy : sy + dy * ts);
+    // next boundary crossings and the entry time of the start cell
+    double tmx = stx > 0 ? ((double)(ci + 1) - sx) * ix : (stx < 0 ? ((double)ci - sx) * ix : INFINITY);
+    double tmy = sty > 0 ? ((double)(cj + 1) - sy) * iy : (sty < 0 ? ((double)cj - sy) * iy : INFINITY);
+    const double tdx = stx ? fabs(ix) : INFINITY, tdy = sty ? fabs(iy) : INFINITY;
+    double t0 = fmax(0.0, fmax(stx ? tmx - tdx : -INFINITY, sty ? tmy - tdy : -INFINITY));
     const int64_t max_steps = (int64_t)(fabs(dx) + fabs(dy)) + 4;  // cells crossed <= |dx| + |dy| + 2
-    for (int64_t s = 0; s < max_steps; ++s) {
-      const double t1 = fmin(fmin(tmx, tmy), 1.0);
-      if (ci == ei && cj == ej) break;  // the point's own cell
-      if (t1 > t0 && ci >= A.oi && ci < A.oi + A.nx && cj >= A.oj && cj < A.oj + A.ny) {
-        const double top = fmax(sz + dz * t0, sz + dz * t1);
-        const int64_t k = store_idx(A, ci, cj);
-        if ((double)h[k] > top + A.margin) {  // NaN compares false
-          h[k] = __int_as_float(0x7fc00000);
-          s2[k] = __int_as_float(0x7fc00000);
+    constexpr int U = 4;
+    bool done = false;
+    for (int64_t s = 0; s < max_steps && !done; s += U) {
+      int64_t kc[U];
+      double top[U];
+      bool act[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        act[u] = false;
+        if (done) continue;
+        const double t1 = fmin(fmin(tmx, tmy), 1.0);
+        if (ci == ei && cj == ej) {  // the point's own cell
+          done = true;
+          continue;
+        }
+        if (t1 > t0 && ci >= A.oi && ci < A.oi + A.nx && cj >= A.oj && cj < A.oj + A.ny) {
+          act[u] = true;
+          kc[u] = store_idx(A, ci, cj);
+          top[u] = fmax(sz + dz * t0, sz + dz * t1);
+        }
+        if (t1 >= 1.0 || t1 >= te) {  // the next cell is entered at or after this segment's end
+          done = true;
+          continue;
+        }
+        if (tmx < tmy) {
+          ci += stx;
+          t0 = tmx;
+          tmx += tdx;
+        } else {
+          cj += sty;
+          t0 = tmy;
+          tmy += tdy;
         }
       }
-      if (t1 >= 1.0) break;
-      if (tmx < tmy) {
-        ci += stx;
-        t0 = tmx;
-        tmx += tdx;
-      } else {
-        cj += sty;
-        t0 = tmy;
-        tmy += tdy;
+      float hv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) hv[u] = act[u] ? h[kc[u]] : __int_as_float(0x7fc00000);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (act[u] && (double)hv[u] > top[u] + A.margin) {  // NaN compares false
+          h[kc[u]] = __int_as_float(0x7fc00000);
+          s2[kc[u]] = __int_as_float(0x7fc00000);
+        }
       }
     }
   }
@@ -228,7 +271,7 @@ __global__ void copy_out_kernel(ElevArgs A, const float* h, const float* s2, flo
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t h, s2, acc, nup, cell, pz, inside, pw, total;
+  size_t h, s2, acc, nup, cell, pz, inside, pw, rinv, total;
 };
 
 Layout layout(const seb_elev_params& p, int64_t np) {
@@ -251,6 +294,8 @@ Layout layout(const seb_elev_params& p, int64_t np) {
   o = align256(o + (size_t)np);
   L.pw = o;
   o = align256(o + (size_t)np * 24);
+  L.rinv = o;
+  o = align256(o + (size_t)np * 16);
   L.total = o;
   return L;
 }
@@ -317,6 +362,7 @@ int seb_elev_create(const seb_elev_params* p, int64_t max_points, void* ws, size
   e->pz = reinterpret_cast<double*>(b + L.pz);
   e->inside = b + L.inside;
   e->pw = reinterpret_cast<double*>(b + L.pw);
+  e->rinv = reinterpret_cast<double*>(b + L.rinv);
   e->oi = e->oj = 0;
   e->valid = false;
   const size_t plane = (size_t)p->nx * p->ny;
@@ -397,8 +443,8 @@ int seb_elev_integrate(seb_elev* e, const seb_scan_pose* pose, const float* pts,
   const int64_t plane = (int64_t)e->p.nx * e->p.ny;
   move_kernel<<<blocks_for(plane), 256, 0, st>>>(A, e->h, e->s2);
   if (n > 0) {
-    points_kernel<<<blocks_for(n), 256, 0, st>>>(A, pts, n, e->cell, e->pz, e->inside, e->pw);
-    raycast_kernel<<<blocks_for(n), 256, 0, st>>>(A, e->pw, e->inside, n, e->h, e->s2);
+    points_kernel<<<blocks_for(n), 256, 0, st>>>(A, pts, n, e->cell, e->pz, e->inside, e->pw, e->rinv);
+    raycast_kernel<<<blocks_for(n * kRaySegs), 256, 0, st>>>(A, e->pw, e->rinv, e->inside, n, e->h, e->s2);
     accumulate_kernel<<<blocks_for(n), 256, 0, st>>>(A, e->cell, e->pz, n, e->h, e->s2, e->acc, e->nup);
     finalize_kernel<<<blocks_for(plane), 256, 0, st>>>(plane, e->h, e->s2, e->acc, e->nup);
   }
