@@ -31,6 +31,8 @@ NX = NY = 400
 K = 72
 RES = 0.05
 LENGTH, WIDTH = 0.9, 0.6
+# local-mapping cycle: the paper's densest configuration (18 x 18 m at 0.1 m, 30 yaw bins)
+CYCLE_SIDE, CYCLE_RES, CYCLE_YAWS = 180, 0.1, 30
 N_SHIFTS = 50
 WORLD = 1200
 WORKLOAD = "se2_map_400x400x72_rebuild_plus_50_shifts"
@@ -508,7 +510,7 @@ def local_mapping_cycle(seb, dev, st, n_scans=6, reps=5):
 
     from synthetic import fractal_world, lidar_scan
 
-    n, K, res = 180, 30, 0.1
+    n, K, res = CYCLE_SIDE, CYCLE_YAWS, CYCLE_RES
     world = fractal_world(7, 700, res=res)
     S_S = np.diag([0.02, 0.02, 0.02]) ** 2
     S_R = np.diag([0.004, 0.004, 0.002]) ** 2
