@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the per-row measurements")
     ap.add_argument("--sur-patches", type=int, default=200_000, help="surrogate training patches")
+    ap.add_argument("--profile-cycle", action="store_true",
+                    help="run only the local-mapping cycle row (the program profiled for its launch list)")
     ap.add_argument("--profile-rebuild", action="store_true",
                     help="only run three full rebuilds of the map (a short program for ncu)")
     return ap.parse_args()
@@ -244,6 +246,14 @@ def main():
     args = parse()
     if args.profile_rebuild:
         return profile_rebuild()
+    if args.profile_cycle:
+        import torch
+
+        import paper_2503_02412_gb300 as seb
+
+        dev = torch.device("cuda", 0)
+        print(json.dumps(local_mapping_cycle(seb, dev, torch.cuda.current_stream(dev))))
+        return None
     if args.impl == "reference":
         return run_reference(args)
     rank, local_rank, world_size = dist_env()
