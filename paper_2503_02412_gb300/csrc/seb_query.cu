@@ -10,9 +10,11 @@
 // grid kernel does; z is the fitted-plane height at (x, y):
 //   z = mean z + (n_x mean px + n_y mean py) / n_z.
 //
-// Layout: a group of GL lanes (8 or 32) owns one pose; lane l takes lattice points
-// l, l + GL, ...; the 10 moment sums are reduced with warp shuffles, and every lane of the
-// group then runs the (cheap) eigen-solve, so no shared memory is needed.
+// Layout: batches of 65,536 poses or more take one pose per thread, streaming its lattice, so
+// a warp runs the eigen-solve, frame and adjoint for 32 poses per pass.  Smaller batches, which
+// would not fill the GPU that way, give a group of GL lanes (8 or 32) to each pose: lane l takes
+// lattice points l, l + GL, ..., the 10 moment sums are reduced with warp shuffles, and every
+// lane of the group then runs the eigen-solve, so no shared memory is needed.
 //
 // Backward (reverse mode, valid set held fixed): g = d loss / d (z, pitch, roll, rough, risk)
 //   - roughness = lambda_min / trace directly; risk: zero on the clamped branches, else w . (kappa/kappa_max, |pitch|/phi_x_max,
@@ -32,7 +34,8 @@
 namespace seb {
 namespace {
 
-constexpr int kPPL = 8;  // lattice points per lane
+constexpr int kPPL = 8;  // lattice points per lane (grouped kernels)
+constexpr int64_t kOneLaneMin = 65536;  // batches this large take one pose per thread
 
 struct QState {
   int N;
@@ -95,47 +98,13 @@ __device__ __forceinline__ void gather(const QTab& Q, const QLaunch& L, int lane
   }
 }
 
-// Moments, eigen-solve, frame and risk of one pose (every lane of the group gets the result).
-template <int GL>
-__device__ __forceinline__ void assess_pose(const QTab& Q, const QLaunch& L, int lane, float c, float s,
-                                            const Pts& P, QState& S) {
+// Eigen-solve, frame and risk of one pose from its moment sums m (N, sum px, sum py, sum z',
+// sum px^2, sum px py, sum py^2, sum px z', sum py z', sum z'^2; z' = z - zref).
+__device__ __forceinline__ void finish_pose(const QTab& Q, const QLaunch& L, const float m[10], float zref,
+                                            float c, float s, QState& S) {
   const float qnan = __int_as_float(0x7fc00000);
-  // Reference height: the known lattice point with the smallest index.
-  int first = 1 << 30;
-  float zf = 0.f;
-#pragma unroll
-  for (int j = kPPL - 1; j >= 0; --j)
-    if (P.ok[j]) {
-      first = lane + j * GL;
-      zf = P.z[j];
-    }
-  const int gfirst = group_min<GL>(first);
-  // broadcast zf from the lane that owns gfirst
-  const int owner = gfirst % GL;
-  const int base = (threadIdx.x & 31) & ~(GL - 1);
-  const float zref = __shfl_sync(0xffffffffu, zf, base + (owner < GL ? owner : 0));
-  float m[10];
-#pragma unroll
-  for (int t = 0; t < 10; ++t) m[t] = 0.f;
-#pragma unroll
-  for (int j = 0; j < kPPL; ++j)
-    if (P.ok[j]) {
-      const float x = P.px[j], y = P.py[j], z = P.z[j] - zref;
-      m[0] += 1.f;
-      m[1] += x;
-      m[2] += y;
-      m[3] += z;
-      m[4] = fmaf(x, x, m[4]);
-      m[5] = fmaf(x, y, m[5]);
-      m[6] = fmaf(y, y, m[6]);
-      m[7] = fmaf(x, z, m[7]);
-      m[8] = fmaf(y, z, m[8]);
-      m[9] = fmaf(z, z, m[9]);
-    }
-#pragma unroll
-  for (int t = 0; t < 10; ++t) m[t] = group_sum<GL>(m[t]);
   S.N = (int)m[0];
-  S.zref = gfirst < (1 << 30) ? zref : 0.f;
+  S.zref = zref;
   S.flags = 0;
   if (S.N < Q.n_min) {
     S.z = S.pitch = S.roll = S.rough = qnan;
@@ -194,6 +163,47 @@ __device__ __forceinline__ void assess_pose(const QTab& Q, const QLaunch& L, int
   }
 }
 
+// Moments, eigen-solve, frame and risk of one pose (every lane of the group gets the result).
+template <int GL>
+__device__ __forceinline__ void assess_pose(const QTab& Q, const QLaunch& L, int lane, float c, float s,
+                                            const Pts& P, QState& S) {
+  // Reference height: the known lattice point with the smallest index.
+  int first = 1 << 30;
+  float zf = 0.f;
+#pragma unroll
+  for (int j = kPPL - 1; j >= 0; --j)
+    if (P.ok[j]) {
+      first = lane + j * GL;
+      zf = P.z[j];
+    }
+  const int gfirst = group_min<GL>(first);
+  // broadcast zf from the lane that owns gfirst
+  const int owner = gfirst % GL;
+  const int base = (threadIdx.x & 31) & ~(GL - 1);
+  const float zref = __shfl_sync(0xffffffffu, zf, base + (owner < GL ? owner : 0));
+  float m[10];
+#pragma unroll
+  for (int t = 0; t < 10; ++t) m[t] = 0.f;
+#pragma unroll
+  for (int j = 0; j < kPPL; ++j)
+    if (P.ok[j]) {
+      const float x = P.px[j], y = P.py[j], z = P.z[j] - zref;
+      m[0] += 1.f;
+      m[1] += x;
+      m[2] += y;
+      m[3] += z;
+      m[4] = fmaf(x, x, m[4]);
+      m[5] = fmaf(x, y, m[5]);
+      m[6] = fmaf(y, y, m[6]);
+      m[7] = fmaf(x, z, m[7]);
+      m[8] = fmaf(y, z, m[8]);
+      m[9] = fmaf(z, z, m[9]);
+    }
+#pragma unroll
+  for (int t = 0; t < 10; ++t) m[t] = group_sum<GL>(m[t]);
+  finish_pose(Q, L, m, gfirst < (1 << 30) ? zref : 0.f, c, s, S);
+}
+
 __device__ __forceinline__ void pose_local(const QLaunch& L, const float* pose, float& xl, float& yl,
                                            float& c, float& s) {
   // Grid coordinate of the pose: cell (col, row) has its centre at ((o + col + 1/2) res).
@@ -203,21 +213,81 @@ __device__ __forceinline__ void pose_local(const QLaunch& L, const float* pose, 
   sincosf(pose[2], &s, &c);
 }
 
-template <typename E, int GL>
-__global__ void __launch_bounds__(256) query_fwd_kernel(const __grid_constant__ QTab Q,
-                                                        const __grid_constant__ QLaunch L) {
-  const int gpb = 256 / GL;
-  const int64_t i = (int64_t)blockIdx.x * gpb + threadIdx.x / GL;
-  const int lane = threadIdx.x & (GL - 1);
-  const bool live = i < L.n;
-  const int64_t ii = live ? i : L.n - 1;  // dead groups mirror the last pose (no store)
-  float xl, yl, c, s;
-  pose_local(L, L.poses + 3 * ii, xl, yl, c, s);
-  Pts P;
-  gather<E, GL>(Q, L, lane, xl, yl, c, s, P);
-  QState S;
-  assess_pose<GL>(Q, L, lane, c, s, P, S);
-  if (!live || lane != 0) return;
+// Pose-level part of the adjoint (known, non-degenerate pose with state S): from the output
+// gradient g[5] to the symmetrised covariance adjoint Sm (dL/dP_i = (Sm e_i + mub) / N for point i
+// with e_i = P_i - mean) and the direct yaw term of the frame.
+__device__ __forceinline__ void pose_adjoint(const QLaunch& L, const QState& S, const float* g, float c, float s,
+                                             float Sm[9], float mub[3], float& th_direct) {
+  const float g0 = g[0];
+  float kb = g[3], pb = g[1], rb = g[2];
+  if (!(S.flags & SEB_FLAG_OBSTACLE)) {
+    const float sp = S.pitch > 0.f ? 1.f : (S.pitch < 0.f ? -1.f : 0.f);
+    const float sr = S.roll > 0.f ? 1.f : (S.roll < 0.f ? -1.f : 0.f);
+    kb += g[4] * L.w0 / L.kappa_max;
+    pb += g[4] * L.w1 * sp / L.phi_x_max;
+    rb += g[4] * L.w2 * sr / L.phi_y_max;
+  }
+  const float* n = S.n;
+  const float uz = n[0] * s - n[1] * c;
+  const float un = sqrtf(n[2] * n[2] + uz * uz);
+  const float yb[3] = {-n[2] * s / un, n[2] * c / un, uz / un};
+  float xb[3];
+  cross(yb, n, xb);
+  const float xbb[3] = {0.f, 0.f, pb * rsqrtf(fmaxf(1.f - xb[2] * xb[2], 1e-30f))};
+  float ybb[3] = {0.f, 0.f, rb * rsqrtf(fmaxf(1.f - yb[2] * yb[2], 1e-30f))};
+  float nb[3] = {0.f, 0.f, 0.f}, t3[3];
+  cross(n, xbb, t3);  // x_b = y_b x n
+  for (int t = 0; t < 3; ++t) ybb[t] += t3[t];
+  cross(xbb, yb, t3);
+  for (int t = 0; t < 3; ++t) nb[t] += t3[t];
+  const float yd = yb[0] * ybb[0] + yb[1] * ybb[1] + yb[2] * ybb[2];
+  float ub[3];
+  for (int t = 0; t < 3; ++t) ub[t] = (ybb[t] - yb[t] * yd) / un;
+  const float xy[3] = {c, s, 0.f};
+  cross(xy, ub, t3);  // u = n x x_yaw
+  for (int t = 0; t < 3; ++t) nb[t] += t3[t];
+  float xyb[3];
+  cross(ub, n, xyb);
+  th_direct = -s * xyb[0] + c * xyb[1];
+  // z = mean z + (n_x mean px + n_y mean py) / n_z
+  const float h = n[0] * S.mu[0] + n[1] * S.mu[1];
+  nb[0] += g0 * S.mu[0] / n[2];
+  nb[1] += g0 * S.mu[1] / n[2];
+  nb[2] -= g0 * h / (n[2] * n[2]);
+  mub[0] = g0 * n[0] / n[2];
+  mub[1] = g0 * n[1] / n[2];
+  mub[2] = g0;
+  // kappa = lambda_min / trace
+  const float tr = S.C[0] + S.C[3] + S.C[5];
+  const float lamb = kb / tr, trb = -kb * S.lam / (tr * tr);
+  float Cb[9];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Cb[3 * a + b] = lamb * n[a] * n[b] + (a == b ? trb : 0.f);
+  // eigenvector part: the other two eigenpairs
+  float l[3];
+  eigvals3<float>(S.C, l);
+  float vmax[3], vmid[3];
+  if (null_vector<float>(S.C, l[2], vmax)) {
+    cross(n, vmax, vmid);
+    const float nm = rsqrtf(vmid[0] * vmid[0] + vmid[1] * vmid[1] + vmid[2] * vmid[2]);
+    for (int t = 0; t < 3; ++t) vmid[t] *= nm;
+    // re-orthogonalise v_max against n and v_mid
+    cross(vmid, n, vmax);
+    const float* vs[2] = {vmid, vmax};
+    const float ls[2] = {l[1], l[2]};
+    for (int jv = 0; jv < 2; ++jv) {
+      const float* v = vs[jv];
+      const float coef = (v[0] * nb[0] + v[1] * nb[1] + v[2] * nb[2]) / (S.lam - ls[jv]);
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) Cb[3 * a + b] += coef * v[a] * n[b];
+    }
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Sm[3 * a + b] = Cb[3 * a + b] + Cb[3 * b + a];
+}
+
+// Outputs and the per-pose state the backward reuses.
+__device__ __forceinline__ void store_pose(const QLaunch& L, int64_t i, const QState& S) {
   float* o = L.out + 5 * i;
   o[0] = S.z;
   o[1] = S.pitch;
@@ -241,6 +311,154 @@ __global__ void __launch_bounds__(256) query_fwd_kernel(const __grid_constant__ 
   }
 }
 
+__device__ __forceinline__ void load_pose(const QLaunch& L, int64_t i, float c, float s, QState& S) {
+  const float* v = L.saved + (int64_t)SEB_QUERY_SAVED * i;
+  S.N = (int)v[0];
+  S.zref = v[1];
+  S.mu[0] = v[2];
+  S.mu[1] = v[3];
+  S.mu[2] = v[4];
+  for (int t = 0; t < 6; ++t) S.C[t] = v[5 + t];
+  S.n[0] = v[11];
+  S.n[1] = v[12];
+  S.n[2] = v[13];
+  S.lam = v[14];
+  S.flags = __float_as_uint(v[15]);
+  if (!(S.flags & (SEB_FLAG_UNKNOWN | SEB_FLAG_DEGENERATE))) {
+    const float* n = S.n;
+    const float uz = n[0] * s - n[1] * c;
+    const float un = sqrtf(n[2] * n[2] + uz * uz);
+    S.roll = asinf(fminf(fmaxf(uz / un, -1.f), 1.f));
+    S.pitch = asinf(fminf(fmaxf(-n[2] * (n[0] * c + n[1] * s) / un, -1.f), 1.f));
+    S.rough = S.lam / (S.C[0] + S.C[3] + S.C[5]);
+  }
+}
+
+// One lattice point of a pose: metric offset, bilinear height and its gradient; false when the
+// point is unknown (a NaN or out-of-window corner).
+template <typename E>
+__device__ __forceinline__ bool lattice_point(const QTab& Q, const QLaunch& L, int q, float xl, float yl, float c,
+                                              float s, float& px, float& py, float& z, float& gx, float& gy) {
+  const E* __restrict__ elev = static_cast<const E*>(L.elev);
+  const float di = (float)Q.di[q], dj = (float)Q.dj[q];
+  const float ox = c * di - s * dj, oy = s * di + c * dj;
+  const float gxc = xl + ox, gyc = yl + oy;
+  const float c0 = floorf(gxc), r0 = floorf(gyc);
+  px = ox * L.res;
+  py = oy * L.res;
+  if (!(c0 >= 0.f && r0 >= 0.f && c0 + 1.f <= (float)(L.nx - 1) && r0 + 1.f <= (float)(L.ny - 1))) return false;
+  const int64_t b = (int64_t)(int)r0 * L.nx + (int)c0;
+  const float z00 = to_f32<E>(elev[b]), z10 = to_f32<E>(elev[b + 1]);
+  const float z01 = to_f32<E>(elev[b + L.nx]), z11 = to_f32<E>(elev[b + L.nx + 1]);
+  if (!(z00 == z00 && z10 == z10 && z01 == z01 && z11 == z11)) return false;
+  const float fx = gxc - c0, fy = gyc - r0, ires = 1.f / L.res;
+  z = (1.f - fx) * (1.f - fy) * z00 + fx * (1.f - fy) * z10 + (1.f - fx) * fy * z01 + fx * fy * z11;
+  gx = ((1.f - fy) * (z10 - z00) + fy * (z11 - z01)) * ires;
+  gy = ((1.f - fx) * (z01 - z00) + fx * (z11 - z10)) * ires;
+  return true;
+}
+
+// Moments of one pose by one thread, streaming its lattice in order (sums centred on the first
+// known point, as the grouped kernels do, but added in lattice order).
+template <typename E>
+__device__ __forceinline__ void stream_moments(const QTab& Q, const QLaunch& L, float xl, float yl, float c, float s,
+                                               float m[10], float& zref) {
+  for (int t = 0; t < 10; ++t) m[t] = 0.f;
+  zref = 0.f;
+  bool have = false;
+  for (int q = 0; q < Q.n; ++q) {
+    float x, y, z, gx, gy;
+    if (!lattice_point<E>(Q, L, q, xl, yl, c, s, x, y, z, gx, gy)) continue;
+    if (!have) {
+      zref = z;
+      have = true;
+    }
+    z -= zref;
+    m[0] += 1.f;
+    m[1] += x;
+    m[2] += y;
+    m[3] += z;
+    m[4] = fmaf(x, x, m[4]);
+    m[5] = fmaf(x, y, m[5]);
+    m[6] = fmaf(y, y, m[6]);
+    m[7] = fmaf(x, z, m[7]);
+    m[8] = fmaf(y, z, m[8]);
+    m[9] = fmaf(z, z, m[9]);
+  }
+}
+
+// One pose per thread, for large batches: a warp then runs the eigen-solve, frame and adjoint
+// for 32 poses per pass (a group of GL lanes per pose runs them for 32 / GL).
+template <typename E>
+__global__ void __launch_bounds__(256) query_fwd1_kernel(const __grid_constant__ QTab Q,
+                                                         const __grid_constant__ QLaunch L) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.n) return;
+  float xl, yl, c, s;
+  pose_local(L, L.poses + 3 * i, xl, yl, c, s);
+  float m[10], zref;
+  stream_moments<E>(Q, L, xl, yl, c, s, m, zref);
+  QState S;
+  finish_pose(Q, L, m, zref, c, s, S);
+  store_pose(L, i, S);
+}
+
+template <typename E>
+__global__ void __launch_bounds__(256) query_bwd1_kernel(const __grid_constant__ QTab Q,
+                                                         const __grid_constant__ QLaunch L) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.n) return;
+  float xl, yl, c, s;
+  pose_local(L, L.poses + 3 * i, xl, yl, c, s);
+  QState S;
+  if (L.saved) {
+    load_pose(L, i, c, s, S);
+  } else {
+    float m[10], zref;
+    stream_moments<E>(Q, L, xl, yl, c, s, m, zref);
+    finish_pose(Q, L, m, zref, c, s, S);
+  }
+  float gpx = 0.f, gpy = 0.f, gth = 0.f;
+  if (!(S.flags & (SEB_FLAG_UNKNOWN | SEB_FLAG_DEGENERATE))) {
+    float Sm[9], mub[3], th_direct;
+    pose_adjoint(L, S, L.gout + 5 * i, c, s, Sm, mub, th_direct);
+    const float iN = 1.f / (float)S.N;
+    for (int q = 0; q < Q.n; ++q) {
+      float px, py, z, gx, gy;
+      if (!lattice_point<E>(Q, L, q, xl, yl, c, s, px, py, z, gx, gy)) continue;
+      const float e0 = px - S.mu[0], e1 = py - S.mu[1], e2 = (z - S.zref) - S.mu[2];
+      const float bx = (Sm[0] * e0 + Sm[1] * e1 + Sm[2] * e2 + mub[0]) * iN;
+      const float by = (Sm[3] * e0 + Sm[4] * e1 + Sm[5] * e2 + mub[1]) * iN;
+      const float bz = (Sm[6] * e0 + Sm[7] * e1 + Sm[8] * e2 + mub[2]) * iN;
+      gpx = fmaf(bz, gx, gpx);
+      gpy = fmaf(bz, gy, gpy);
+      gth += -bx * py + by * px + bz * (-gx * py + gy * px);
+    }
+    gth += th_direct;
+  }
+  L.gpose[3 * i] = gpx;
+  L.gpose[3 * i + 1] = gpy;
+  L.gpose[3 * i + 2] = gth;
+}
+
+template <typename E, int GL>
+__global__ void __launch_bounds__(256) query_fwd_kernel(const __grid_constant__ QTab Q,
+                                                        const __grid_constant__ QLaunch L) {
+  const int gpb = 256 / GL;
+  const int64_t i = (int64_t)blockIdx.x * gpb + threadIdx.x / GL;
+  const int lane = threadIdx.x & (GL - 1);
+  const bool live = i < L.n;
+  const int64_t ii = live ? i : L.n - 1;  // dead groups mirror the last pose (no store)
+  float xl, yl, c, s;
+  pose_local(L, L.poses + 3 * ii, xl, yl, c, s);
+  Pts P;
+  gather<E, GL>(Q, L, lane, xl, yl, c, s, P);
+  QState S;
+  assess_pose<GL>(Q, L, lane, c, s, P, S);
+  if (!live || lane != 0) return;
+  store_pose(L, i, S);
+}
+
 template <typename E, int GL>
 __global__ void __launch_bounds__(256) query_bwd_kernel(const __grid_constant__ QTab Q,
                                                         const __grid_constant__ QLaunch L) {
@@ -254,98 +472,14 @@ __global__ void __launch_bounds__(256) query_bwd_kernel(const __grid_constant__ 
   Pts P;
   gather<E, GL>(Q, L, lane, xl, yl, c, s, P);
   QState S;
-  if (L.saved) {
-    const float* v = L.saved + (int64_t)SEB_QUERY_SAVED * ii;
-    S.N = (int)v[0];
-    S.zref = v[1];
-    S.mu[0] = v[2];
-    S.mu[1] = v[3];
-    S.mu[2] = v[4];
-    for (int t = 0; t < 6; ++t) S.C[t] = v[5 + t];
-    S.n[0] = v[11];
-    S.n[1] = v[12];
-    S.n[2] = v[13];
-    S.lam = v[14];
-    S.flags = __float_as_uint(v[15]);
-    if (!(S.flags & (SEB_FLAG_UNKNOWN | SEB_FLAG_DEGENERATE))) {
-      const float* n = S.n;
-      const float uz = n[0] * s - n[1] * c;
-      const float un = sqrtf(n[2] * n[2] + uz * uz);
-      S.roll = asinf(fminf(fmaxf(uz / un, -1.f), 1.f));
-      S.pitch = asinf(fminf(fmaxf(-n[2] * (n[0] * c + n[1] * s) / un, -1.f), 1.f));
-      S.rough = S.lam / (S.C[0] + S.C[3] + S.C[5]);
-    }
-  } else {
+  if (L.saved)
+    load_pose(L, ii, c, s, S);
+  else
     assess_pose<GL>(Q, L, lane, c, s, P, S);
-  }
   float gpx = 0.f, gpy = 0.f, gth = 0.f;
   if (!(S.flags & (SEB_FLAG_UNKNOWN | SEB_FLAG_DEGENERATE))) {
-    const float* g = L.gout + 5 * ii;
-    const float g0 = g[0];
-    float kb = g[3], pb = g[1], rb = g[2];
-    if (!(S.flags & SEB_FLAG_OBSTACLE)) {
-      const float sp = S.pitch > 0.f ? 1.f : (S.pitch < 0.f ? -1.f : 0.f);
-      const float sr = S.roll > 0.f ? 1.f : (S.roll < 0.f ? -1.f : 0.f);
-      kb += g[4] * L.w0 / L.kappa_max;
-      pb += g[4] * L.w1 * sp / L.phi_x_max;
-      rb += g[4] * L.w2 * sr / L.phi_y_max;
-    }
-    const float* n = S.n;
-    const float uz = n[0] * s - n[1] * c;
-    const float un = sqrtf(n[2] * n[2] + uz * uz);
-    const float yb[3] = {-n[2] * s / un, n[2] * c / un, uz / un};
-    float xb[3];
-    cross(yb, n, xb);
-    const float xbb[3] = {0.f, 0.f, pb * rsqrtf(fmaxf(1.f - xb[2] * xb[2], 1e-30f))};
-    float ybb[3] = {0.f, 0.f, rb * rsqrtf(fmaxf(1.f - yb[2] * yb[2], 1e-30f))};
-    float nb[3] = {0.f, 0.f, 0.f}, t3[3];
-    cross(n, xbb, t3);  // x_b = y_b x n
-    for (int t = 0; t < 3; ++t) ybb[t] += t3[t];
-    cross(xbb, yb, t3);
-    for (int t = 0; t < 3; ++t) nb[t] += t3[t];
-    const float yd = yb[0] * ybb[0] + yb[1] * ybb[1] + yb[2] * ybb[2];
-    float ub[3];
-    for (int t = 0; t < 3; ++t) ub[t] = (ybb[t] - yb[t] * yd) / un;
-    const float xy[3] = {c, s, 0.f};
-    cross(xy, ub, t3);  // u = n x x_yaw
-    for (int t = 0; t < 3; ++t) nb[t] += t3[t];
-    float xyb[3];
-    cross(ub, n, xyb);
-    const float th_direct = -s * xyb[0] + c * xyb[1];
-    // z = mean z + (n_x mean px + n_y mean py) / n_z
-    const float h = n[0] * S.mu[0] + n[1] * S.mu[1];
-    nb[0] += g0 * S.mu[0] / n[2];
-    nb[1] += g0 * S.mu[1] / n[2];
-    nb[2] -= g0 * h / (n[2] * n[2]);
-    const float mub[3] = {g0 * n[0] / n[2], g0 * n[1] / n[2], g0};
-    // kappa = lambda_min / trace
-    const float tr = S.C[0] + S.C[3] + S.C[5];
-    const float lamb = kb / tr, trb = -kb * S.lam / (tr * tr);
-    float Cb[9];
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) Cb[3 * a + b] = lamb * n[a] * n[b] + (a == b ? trb : 0.f);
-    // eigenvector part: the other two eigenpairs
-    float l[3];
-    eigvals3<float>(S.C, l);
-    float vmax[3], vmid[3];
-    if (null_vector<float>(S.C, l[2], vmax)) {
-      cross(n, vmax, vmid);
-      const float nm = rsqrtf(vmid[0] * vmid[0] + vmid[1] * vmid[1] + vmid[2] * vmid[2]);
-      for (int t = 0; t < 3; ++t) vmid[t] *= nm;
-      // re-orthogonalise v_max against n and v_mid
-      cross(vmid, n, vmax);
-      const float* vs[2] = {vmid, vmax};
-      const float ls[2] = {l[1], l[2]};
-      for (int jv = 0; jv < 2; ++jv) {
-        const float* v = vs[jv];
-        const float coef = (v[0] * nb[0] + v[1] * nb[1] + v[2] * nb[2]) / (S.lam - ls[jv]);
-        for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b) Cb[3 * a + b] += coef * v[a] * n[b];
-      }
-    }
-    float Sm[9];
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) Sm[3 * a + b] = Cb[3 * a + b] + Cb[3 * b + a];
+    float Sm[9], mub[3], th_direct;
+    pose_adjoint(L, S, L.gout + 5 * ii, c, s, Sm, mub, th_direct);
     const float iN = 1.f / (float)S.N;
 #pragma unroll
     for (int j = 0; j < kPPL; ++j) {
@@ -373,6 +507,15 @@ __global__ void __launch_bounds__(256) query_bwd_kernel(const __grid_constant__ 
 template <typename E>
 cudaError_t launch_q(const QTab& Q, const QLaunch& L, bool backward, cudaStream_t st) {
   if (L.n == 0) return cudaSuccess;
+  if (L.n >= kOneLaneMin) {  // enough poses to fill the GPU with one pose per thread
+    const int64_t blocks = (L.n + 255) / 256;
+    if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+    if (backward)
+      query_bwd1_kernel<E><<<(unsigned)blocks, 256, 0, st>>>(Q, L);
+    else
+      query_fwd1_kernel<E><<<(unsigned)blocks, 256, 0, st>>>(Q, L);
+    return cudaGetLastError();
+  }
   const int GL = Q.n <= 8 * kPPL ? 8 : 32;
   const int gpb = 256 / GL;
   const int64_t blocks = (L.n + gpb - 1) / gpb;

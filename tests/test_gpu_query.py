@@ -201,3 +201,45 @@ def test_large_batch_and_empty(seb):
     r, rf = oracle.query_poses(oracle.OracleParams(**C1), e.cpu().numpy().astype(np.float64),
                                poses.cpu().numpy()[idx].astype(np.float64))
     compare(out.cpu().numpy()[idx], fl.cpu().numpy()[idx], r, rf, label="1M sample")
+
+
+def test_one_pose_per_thread_kernels(seb):
+    """Batches of 65,536 poses or more take the one-pose-per-thread kernels: their backward
+    against the FP64 oracle adjoint on a sample, the saved state against recomputation, and both
+    directions against the grouped kernels that the first 4,096 poses take when run alone (the
+    moment sums are added in a different order, so agreement is to FP32 rounding)."""
+    from paper_2503_02412_gb300 import abi
+
+    cfg = dict(C1, kappa_max=1.0, phi_x_max=1.4, phi_y_max=1.4)
+    e = bumpy_plane(13)
+    n = 70_000
+    poses = random_poses(14, n, 100, 100, 0.1, 5)
+    gout = np.random.default_rng(15).normal(size=(n, 5))
+    g, out, fl = _bwd(seb, cfg, e, poses, gout)
+    gs, outs, fls = _bwd(seb, cfg, e, poses[:4096], gout[:4096])
+    ok = ((fl[:4096] & 5) == 0) & (fl[:4096] == fls)
+    assert ok.mean() > 0.9
+    assert np.abs(out[:4096][ok] - outs[ok]).max() < 2e-5
+    scale = np.abs(gs[ok]).max(axis=0)
+    assert (np.abs(g[:4096] - gs)[ok] / scale).max() < 1e-3
+    idx = np.random.default_rng(16).integers(0, n, 2000)
+    r = oracle.query_poses_vjp(oracle.OracleParams(**cfg), e.astype(np.float64), poses[idx].astype(np.float64),
+                               gout[idx])
+    sel = (fl[idx] & 5) == 0
+    sc = np.abs(r[sel]).max(axis=0)
+    assert (np.abs(g[idx] - r)[sel] / sc).max() < 1e-3
+    # saved state versus recomputation in the backward
+    p = seb.SebParams(**cfg).c()
+    te = torch.from_numpy(e).cuda()
+    tp = torch.from_numpy(poses).cuda()
+    st = torch.cuda.current_stream().cuda_stream
+    o = torch.empty(n, 5, device="cuda")
+    f = torch.empty(n, dtype=torch.uint8, device="cuda")
+    sv = torch.empty(n, 16, device="cuda")
+    abi.seb_query_poses(p, te.data_ptr(), 0, 0, tp.data_ptr(), n, o.data_ptr(), f.data_ptr(), sv.data_ptr(), st)
+    go = torch.from_numpy(gout.astype(np.float32)).cuda()
+    a = torch.empty(n, 3, device="cuda")
+    b = torch.empty(n, 3, device="cuda")
+    abi.seb_query_poses_backward(p, te.data_ptr(), 0, 0, tp.data_ptr(), sv.data_ptr(), go.data_ptr(), a.data_ptr(), n, st)
+    abi.seb_query_poses_backward(p, te.data_ptr(), 0, 0, tp.data_ptr(), 0, go.data_ptr(), b.data_ptr(), n, st)
+    assert torch.allclose(a, b, rtol=1e-5, atol=1e-6)
