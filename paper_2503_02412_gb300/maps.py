@@ -107,11 +107,18 @@ class SebMap:
     def view(self):
         return abi.seb_map_view(self.handle)
 
-    def outputs(self):
-        """Logical-order copy: (out [5][K][ny][nx] float32, flags [K][ny][nx] uint8)."""
+    def outputs(self, out: torch.Tensor = None, fl: torch.Tensor = None):
+        """Logical-order copy: (out [5][K][ny][nx] float32, flags [K][ny][nx] uint8), into the
+        given contiguous tensors when provided."""
         p = self.params
-        out = torch.empty((5, p.n_yaw, p.ny, p.nx), dtype=torch.float32, device=self.device)
-        fl = torch.empty((p.n_yaw, p.ny, p.nx), dtype=torch.uint8, device=self.device)
+        if out is None:
+            out = torch.empty((5, p.n_yaw, p.ny, p.nx), dtype=torch.float32, device=self.device)
+        if fl is None:
+            fl = torch.empty((p.n_yaw, p.ny, p.nx), dtype=torch.uint8, device=self.device)
+        if tuple(out.shape) != (5, p.n_yaw, p.ny, p.nx) or not out.is_contiguous() or out.dtype != torch.float32:
+            raise ValueError("out must be a contiguous float32 tensor [5, n_yaw, ny, nx]")
+        if tuple(fl.shape) != (p.n_yaw, p.ny, p.nx) or not fl.is_contiguous() or fl.dtype != torch.uint8:
+            raise ValueError("flags must be a contiguous uint8 tensor [n_yaw, ny, nx]")
         abi.seb_map_set_stream(self.handle, _stream(self.device))
         abi.seb_map_copy_out(self.handle, out.data_ptr(), fl.data_ptr())
         return out, fl
