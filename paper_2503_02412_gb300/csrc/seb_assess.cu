@@ -508,16 +508,21 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int len = hi - lo + 1;
     const float flo = (float)lo, fhi = (float)hi;
     float2 A[4], B[4], C[4];
+    // Column 0 of the block: A = sum z', C = sum z'^2 and Tb = sum of the running sums of z'
+    // = sum (len - k) z'_k, so that sum p z' = (hi + 1) A - Tb with p = lo + k.
+    const float h1 = fhi + 1.f;
+    const float2 H2 = f2(h1, h1);
+    float2 Bx;
     if (!masked) {
-      float2 Ab = zero2, Bx = zero2, Cb = zero2, pf = f2(flo, flo);
+      float2 Ab = zero2, Tb = zero2, Cb = zero2;
 #pragma unroll 4
       for (int k = 0; k < len; ++k) {
         const float2 zp = add2(pq[k], nref);
         Ab = add2(Ab, zp);
-        Bx = fma2(pf, zp, Bx);
+        Tb = add2(Tb, Ab);
         Cb = fma2(zp, zp, Cb);
-        pf = add2(pf, one2);
       }
+      Bx = fma2(H2, Ab, neg2(Tb));
       A[0] = Ab;
       B[0] = Bx;
       C[0] = Cb;
@@ -539,20 +544,34 @@ __global__ void __launch_bounds__(kThreads, 2)
         zp = fma2(nref, m, f2(kx ? v.x : 0.f, ky ? v.y : 0.f));
         x = f2(kx ? 0.f : 1.f, ky ? 0.f : 1.f);
       };
-      float2 Ab = zero2, Bx = zero2, Cb = zero2, pf = f2(flo, flo);
-      float2 qn = zero2, qx = zero2, qxx = zero2;
+      // Known weights summed three times over (k1 = sum m, k2 = sum (len - k) m_k,
+      // k3 = sum (len - k)(len - k + 1) / 2 m_k); with u = len - k the missing moments are
+      // X1 = len - k1, X2 = sum u x = len (len + 1) / 2 - k2, X3 = len (len + 1)(len + 2) / 6 - k3,
+      // and p = hi + 1 - u gives qx = (hi + 1) X1 - X2, qxx = (hi + 1)^2 X1 - 2 (hi + 1) X2 + 2 X3 - X2.
+      // Every term is an integer below 2^24, so all of it is exact.
+      float2 Ab = zero2, Tb = zero2, Cb = zero2;
+      float2 k1 = zero2, k2 = zero2, k3 = zero2;
 #pragma unroll 2
       for (int k = 0; k < len; ++k) {
-        float2 zp, x;
-        zof(k, zp, x);
+        const float2 v = pq[k];
+        const bool kx = v.x == v.x, ky = v.y == v.y;
+        const float2 m = f2(kx ? 1.f : 0.f, ky ? 1.f : 0.f);
+        const float2 zp = fma2(nref, m, f2(kx ? v.x : 0.f, ky ? v.y : 0.f));
         Ab = add2(Ab, zp);
-        Bx = fma2(pf, zp, Bx);
+        Tb = add2(Tb, Ab);
         Cb = fma2(zp, zp, Cb);
-        qn = add2(qn, x);
-        qx = fma2(pf, x, qx);
-        qxx = fma2(__fmul2_rn(pf, pf), x, qxx);
-        pf = add2(pf, one2);
+        k1 = add2(k1, m);
+        k2 = add2(k2, k1);
+        k3 = add2(k3, k2);
       }
+      Bx = fma2(H2, Ab, neg2(Tb));
+      const float fl = (float)len;
+      const float t1 = fl, t2 = fl * (fl + 1.f) * 0.5f, t3 = (float)(len * (len + 1) * (len + 2) / 6);
+      const float2 X1 = add2(f2(t1, t1), neg2(k1)), X2 = add2(f2(t2, t2), neg2(k2)),
+                   X3 = add2(f2(t3, t3), neg2(k3));
+      float2 qn = X1;
+      float2 qx = fma2(H2, X1, neg2(X2));
+      float2 qxx = add2(fma2(__fmul2_rn(H2, H2), X1, fma2(f2(-2.f * h1, -2.f * h1), X2, add2(X3, X3))), neg2(X2));
       A[0] = Ab;
       B[0] = Bx;
       C[0] = Cb;
