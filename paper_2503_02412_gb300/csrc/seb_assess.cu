@@ -447,14 +447,24 @@ __global__ void __launch_bounds__(kThreads, 2)
   __syncthreads();
   const E* __restrict__ elev = static_cast<const E*>(L.elev);
   const float qnan = __int_as_float(0x7fc00000);
-  for (int idx = tid; idx < sw * sh; idx += kThreads) {
-    const int row = idx / sw, col = idx - row * sw;
-    const int gy = ty0 - ry + row, gx = tx0 - rx + col;
-    float v = qnan;
-    if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) v = to_f32<E>(elev[(int64_t)gy * L.nx + gx]);
-    if (v != v) rowflag[row] = 1;
-    if (row < sh - 1) pt[sl_index(row, col, sw2)].x = v;
-    if (row > 0) pt[sl_index(row - 1, col, sw2)].y = v;
+  {
+    // row-major walk of the staged tile in steps of kThreads cells (dc < sw, so one carry)
+    const int dr = kThreads / sw, dc = kThreads - dr * sw;
+    int row = tid / sw, col = tid - (tid / sw) * sw;
+    while (row < sh) {
+      const int gy = ty0 - ry + row, gx = tx0 - rx + col;
+      float v = qnan;
+      if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) v = to_f32<E>(elev[(int64_t)gy * L.nx + gx]);
+      if (v != v) rowflag[row] = 1;
+      if (row < sh - 1) pt[sl_index(row, col, sw2)].x = v;
+      if (row > 0) pt[sl_index(row - 1, col, sw2)].y = v;
+      row += dr;
+      col += dc;
+      if (col >= sw) {
+        col -= sw;
+        ++row;
+      }
+    }
   }
   __syncthreads();
 
@@ -494,9 +504,14 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
   const float2 nref = f2(-ref, -ref), one2 = f2(1.f, 1.f), zero2 = f2(0.f, 0.f);
 
-  float2 S0[4], S1[4], S2[4], S3[4];
+  // Sums over the runs: column 0 of the block (S0c = sum z', S1c = sum p z', S2c = sum dj z',
+  // S3c = sum z'^2) and, for t = 1..3, the sums of what the slide from column t - 1 to column t
+  // adds (D0 = z'_in - z'_out, D1 = p_in z'_in - p_out z'_out, D2 = dj D0, D3 = z'_in^2 - z'_out^2).
+  // Column g is then column 0 plus the slides 1..g; its x-offsets are di = p - g.
+  float2 S0c = zero2, S1c = zero2, S2c = zero2, S3c = zero2;
+  float2 D0[3], D1[3], D2[3], D3[3];
 #pragma unroll
-  for (int g = 0; g < 4; ++g) S0[g] = S1[g] = S2[g] = S3[g] = zero2;
+  for (int t = 0; t < 3; ++t) D0[t] = D1[t] = D2[t] = D3[t] = zero2;
   auto Qs = [&](int k, int g) -> float2& { return qs[(k * 4 + g) * kThreads + tid]; };
 
   for (int q = r0; q < r1; ++q) {
@@ -507,12 +522,25 @@ __global__ void __launch_bounds__(kThreads, 2)
     const float2* pq = pt + sl_index(row, rx + lx + lo, sw2);  // pq[k]: column lo + k of the block
     const int len = hi - lo + 1;
     const float flo = (float)lo, fhi = (float)hi;
-    float2 A[4], B[4], C[4];
+    const float2 dj2 = f2((float)dj, (float)dj);
+    auto slide = [&](int t, float2 zo, float2 zi) {
+      const float po = flo + (float)t, pi = fhi + (float)(t + 1);
+      const float2 d = add2(zi, neg2(zo));
+      D0[t] = add2(D0[t], d);
+      D2[t] = fma2(dj2, d, D2[t]);
+      D1[t] = fma2(f2(pi, pi), zi, fma2(f2(-po, -po), zo, D1[t]));
+      D3[t] = fma2(zi, zi, fma2(neg2(zo), zo, D3[t]));
+    };
+    auto column0 = [&](float2 Ab, float2 Bx, float2 Cb) {
+      S0c = add2(S0c, Ab);
+      S1c = add2(S1c, Bx);
+      S2c = fma2(dj2, Ab, S2c);
+      S3c = add2(S3c, Cb);
+    };
     // Column 0 of the block: A = sum z', C = sum z'^2 and Tb = sum of the running sums of z'
     // = sum (len - k) z'_k, so that sum p z' = (hi + 1) A - Tb with p = lo + k.
     const float h1 = fhi + 1.f;
     const float2 H2 = f2(h1, h1);
-    float2 Bx;
     if (!masked) {
       float2 Ab = zero2, Tb = zero2, Cb = zero2;
 #pragma unroll 4
@@ -522,19 +550,9 @@ __global__ void __launch_bounds__(kThreads, 2)
         Tb = add2(Tb, Ab);
         Cb = fma2(zp, zp, Cb);
       }
-      Bx = fma2(H2, Ab, neg2(Tb));
-      A[0] = Ab;
-      B[0] = Bx;
-      C[0] = Cb;
+      column0(Ab, fma2(H2, Ab, neg2(Tb)), Cb);
 #pragma unroll
-      for (int g = 1; g < 4; ++g) {
-        const float2 zo = add2(pq[g - 1], nref), zi = add2(pq[len - 1 + g], nref);
-        const float po = flo + (float)(g - 1), pi = fhi + (float)g;
-        A[g] = add2(add2(A[g - 1], neg2(zo)), zi);
-        Bx = fma2(f2(pi, pi), zi, fma2(f2(-po, -po), zo, Bx));
-        C[g] = fma2(zi, zi, fma2(neg2(zo), zo, C[g - 1]));
-        B[g] = fma2(f2(-(float)g, -(float)g), A[g], Bx);
-      }
+      for (int t = 0; t < 3; ++t) slide(t, add2(pq[t], nref), add2(pq[len + t], nref));
     } else {
       // unknown heights: weight m = 0, z' = fma(-ref, m, z) = 0; x = 1 - m counts them
       auto zof = [&](int k, float2& zp, float2& x) {
@@ -564,7 +582,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         k2 = add2(k2, k1);
         k3 = add2(k3, k2);
       }
-      Bx = fma2(H2, Ab, neg2(Tb));
+      column0(Ab, fma2(H2, Ab, neg2(Tb)), Cb);
       const float fl = (float)len;
       const float t1 = fl, t2 = fl * (fl + 1.f) * 0.5f, t3 = (float)(len * (len + 1) * (len + 2) / 6);
       const float2 X1 = add2(f2(t1, t1), neg2(k1)), X2 = add2(f2(t2, t2), neg2(k2)),
@@ -572,23 +590,17 @@ __global__ void __launch_bounds__(kThreads, 2)
       float2 qn = X1;
       float2 qx = fma2(H2, X1, neg2(X2));
       float2 qxx = add2(fma2(__fmul2_rn(H2, H2), X1, fma2(f2(-2.f * h1, -2.f * h1), X2, add2(X3, X3))), neg2(X2));
-      A[0] = Ab;
-      B[0] = Bx;
-      C[0] = Cb;
       const float fdj = (float)dj;
-      const float2 dj2 = f2(fdj, fdj), dj22 = f2(fdj * fdj, fdj * fdj);
+      const float2 dj22 = f2(fdj * fdj, fdj * fdj);
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
         if (g > 0) {
           float2 zo, xo, zi, xi;
           zof(g - 1, zo, xo);
           zof(len - 1 + g, zi, xi);
+          slide(g - 1, zo, zi);
           const float po = flo + (float)(g - 1), pi = fhi + (float)g;
           const float2 po2 = f2(po, po), pi2 = f2(pi, pi);
-          A[g] = add2(add2(A[g - 1], neg2(zo)), zi);
-          Bx = fma2(pi2, zi, fma2(neg2(po2), zo, Bx));
-          C[g] = fma2(zi, zi, fma2(neg2(zo), zo, C[g - 1]));
-          B[g] = fma2(f2(-(float)g, -(float)g), A[g], Bx);
           qn = add2(add2(qn, neg2(xo)), xi);
           qx = fma2(pi2, xi, fma2(neg2(po2), xo, qx));
           qxx = fma2(__fmul2_rn(pi2, pi2), xi, fma2(neg2(__fmul2_rn(po2, po2)), xo, qxx));
@@ -605,13 +617,22 @@ __global__ void __launch_bounds__(kThreads, 2)
         Qs(5, g) = fma2(dj22, qn, Qs(5, g));
       }
     }
-    const float2 dj2 = f2((float)dj, (float)dj);
+  }
+  float2 S0[4], S1[4], S2[4], S3[4];
+  {
+    float2 a = S0c, bx = S1c, c2 = S2c, c3 = S3c;
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
-      S0[g] = add2(S0[g], A[g]);
-      S1[g] = add2(S1[g], B[g]);
-      S2[g] = fma2(dj2, A[g], S2[g]);
-      S3[g] = add2(S3[g], C[g]);
+      if (g > 0) {
+        a = add2(a, D0[g - 1]);
+        bx = add2(bx, D1[g - 1]);
+        c2 = add2(c2, D2[g - 1]);
+        c3 = add2(c3, D3[g - 1]);
+      }
+      S0[g] = a;
+      S1[g] = fma2(f2(-(float)g, -(float)g), a, bx);
+      S2[g] = c2;
+      S3[g] = c3;
     }
   }
 
