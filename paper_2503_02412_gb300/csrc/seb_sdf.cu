@@ -15,11 +15,11 @@
 //   1. cols_kernel: sweeps every column down and up (linear time), split in 8 row segments swept
 //      by separate warps and joined through their first / last obstacle and free rows, and
 //      stores per cell the distance in rows to the nearest obstacle and to the nearest free cell
-//      of its column (uint16 each, 0xFFFF = none within W).
-//   2. rows_kernel: a block per (bin, row) stages that row's column distances in shared
-//      memory; every cell takes the minimum of g(j')^2 + (j - j')^2 over |j - j'| = 0, 1, 2, ...
-//      and stops when (j - j')^2 alone reaches the best value.  The squared distances are
-//      exact 32-bit integers.
+//      of its column (uint16 each, 0xFFFF = none within W).  Loads are issued 8 rows at a time.
+//   2. rows_kernel: a block per (bin, row) stages that row's squared column distances in shared
+//      memory, padded with "no feature" sentinels; every cell takes the minimum of
+//      g(j')^2 + (j - j')^2 over |j - j'| = 0, 1, 2, ..., four offsets per step, and stops when
+//      (j - j')^2 alone reaches the best value.  The squared distances are exact 32-bit integers.
 #include <cuda_runtime.h>
 #include <limits.h>
 #include <math.h>
@@ -34,7 +34,9 @@ constexpr uint32_t kNone = 0xFFFFu;
 constexpr int kMaxSide = 16384;
 constexpr int kSegs = 8;
 constexpr int kColThreads = 32 * kSegs;
+constexpr int kBatch = 8;      // column-pass loads in flight per thread
 constexpr int kRowThreads = 256;
+constexpr size_t kPadSmemMax = 96 * 1024;  // padded row pass up to this much shared memory
 constexpr int32_t kFar = 1 << 30;  // "no feature": above any W^2 (W <= 16384), kFar + W^2 < 2^31
 
 struct SdfArgs {
@@ -66,19 +68,27 @@ __global__ void __launch_bounds__(kColThreads) cols_kernel(const SdfArgs A) {
   uint32_t* out = A.work + (int64_t)k * A.ny * A.nx + j;
   int last_o = -1, first_o = -1, last_f = -1, first_f = -1;
   if (col) {
-#pragma unroll 4
-    for (int i = i0; i < i1; ++i) {
-      const bool ob = !(__ldg(A.risk + phys(A, k, i, j)) < A.thr);  // NaN: obstacle
-      if (ob) {
-        last_o = i;
-        first_o = first_o < 0 ? i : first_o;
-      } else {
-        last_f = i;
-        first_f = first_f < 0 ? i : first_f;
+    // kBatch loads in flight before the batch's stores (the stores could alias the loads)
+    for (int ib = i0; ib < i1; ib += kBatch) {
+      float v[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) v[u] = ib + u < i1 ? __ldg(A.risk + phys(A, k, ib + u, j)) : 0.f;
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int i = ib + u;
+        if (i >= i1) break;
+        const bool ob = !(v[u] < A.thr);  // NaN: obstacle
+        if (ob) {
+          last_o = i;
+          first_o = first_o < 0 ? i : first_o;
+        } else {
+          last_f = i;
+          first_f = first_f < 0 ? i : first_f;
+        }
+        const uint32_t uo = last_o < 0 ? kNone : (uint32_t)(i - last_o);
+        const uint32_t uf = last_f < 0 ? kNone : (uint32_t)(i - last_f);
+        out[(int64_t)i * A.nx] = (uo << 16) | uf;
       }
-      const uint32_t uo = last_o < 0 ? kNone : (uint32_t)(i - last_o);
-      const uint32_t uf = last_f < 0 ? kNone : (uint32_t)(i - last_f);
-      out[(int64_t)i * A.nx] = (uo << 16) | uf;
     }
   }
   seg_rows[seg][0][lane] = last_o;
@@ -102,46 +112,79 @@ __global__ void __launch_bounds__(kColThreads) cols_kernel(const SdfArgs A) {
     if (next != INT_MAX) d = min(d, next - i);
     return d > W ? kNone : (uint32_t)d;
   };
-#pragma unroll 4
-  for (int i = i1 - 1; i >= i0; --i) {
-    const uint32_t v = out[(int64_t)i * A.nx];
-    const uint32_t uo = v >> 16, uf = v & 0xFFFFu;
-    if (uo == 0) next_o = i;
-    if (uf == 0) next_f = i;
-    out[(int64_t)i * A.nx] = (fin(uo, above_o, next_o, i) << 16) | fin(uf, above_f, next_f, i);
+  for (int ib = i1 - 1; ib >= i0; ib -= kBatch) {
+    uint32_t w[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) w[u] = ib - u >= i0 ? out[(int64_t)(ib - u) * A.nx] : 0u;
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int i = ib - u;
+      if (i < i0) break;
+      const uint32_t uo = w[u] >> 16, uf = w[u] & 0xFFFFu;
+      if (uo == 0) next_o = i;
+      if (uf == 0) next_f = i;
+      out[(int64_t)i * A.nx] = (fin(uo, above_o, next_o, i) << 16) | fin(uf, above_f, next_f, i);
+    }
   }
 }
 
-__global__ void __launch_bounds__(kRowThreads) rows_kernel(const SdfArgs A) {
-  extern __shared__ int32_t gsq[];  // [2][nx]: squared column distances to obstacles, to free cells
+template <bool PAD>
+__global__ void __launch_bounds__(kRowThreads) rows_kernel(const SdfArgs A, int P) {
+  // squared column distances to obstacles and to free cells, [2][nx]; with PAD each row carries
+  // P "no feature" sentinels on both sides ([2][P + nx + P]), so that the search reads no index
+  // out of range without clamping it
+  extern __shared__ int32_t gsq[];
   const int k = blockIdx.x / A.ny, i = blockIdx.x - k * A.ny;
-  const uint32_t* row = A.work + ((int64_t)k * A.ny + i) * A.nx;
-  int32_t* go2 = gsq;
-  int32_t* gf2 = gsq + A.nx;
-  for (int j = threadIdx.x; j < A.nx; j += blockDim.x) {
-    const uint32_t v = row[j];
-    const int32_t o = (int32_t)(v >> 16), f = (int32_t)(v & 0xFFFFu);
-    go2[j] = o == (int32_t)kNone ? kFar : o * o;
-    gf2[j] = f == (int32_t)kNone ? kFar : f * f;
+  const int nx = A.nx, stride = PAD ? nx + 2 * P : nx, off = PAD ? P : 0;
+  const uint32_t* row = A.work + ((int64_t)k * A.ny + i) * nx;
+  for (int t = threadIdx.x; t < stride; t += blockDim.x) {
+    const int j = t - off;
+    int32_t o = kFar, f = kFar;
+    if (j >= 0 && j < nx) {
+      const uint32_t v = row[j];
+      const int32_t uo = (int32_t)(v >> 16), uf = (int32_t)(v & 0xFFFFu);
+      o = uo == (int32_t)kNone ? kFar : uo * uo;
+      f = uf == (int32_t)kNone ? kFar : uf * uf;
+    }
+    gsq[t] = o;
+    gsq[stride + t] = f;
   }
   __syncthreads();
-  // squared distances stay below W^2 + kFar < 2^31: 32-bit integers (64-bit ones are emulated)
+  const int32_t* go2 = gsq + off;
+  const int32_t* gf2 = gsq + stride + off;
+  // squared distances stay below (nx + P)^2 + kFar < 2^31: 32-bit integers
   const int32_t W2 = A.W * A.W;
-  for (int j = threadIdx.x; j < A.nx; j += blockDim.x) {
+  const int last = nx - 1;
+  for (int j = threadIdx.x; j < nx; j += blockDim.x) {
     const bool obst = go2[j] == 0;
     const int32_t* h = obst ? gf2 : go2;  // obstacle cells search the free cells, and the reverse
     int32_t best = h[j];
-    const int lim = min(A.W, max(j, A.nx - 1 - j)), last = A.nx - 1;
-    // Offsets past a row end re-read the end column at an overstated distance (its true offset
-    // was already counted), which cannot lower the minimum: the indices are clamped instead of
-    // tested.  Two offsets per step; the early exit is checked before each pair.
-    for (int s = 1; s <= lim; s += 2) {
-      const int32_t s2 = s * s;
-      if (s2 >= best) break;  // every farther column is at least s^2 away
-      const int32_t t2 = s2 + 2 * s + 1;
-      const int32_t a0 = h[max(j - s, 0)], b0 = h[min(j + s, last)];
-      const int32_t a1 = h[max(j - s - 1, 0)], b1 = h[min(j + s + 1, last)];
-      best = min(best, min(s2 + min(a0, b0), t2 + min(a1, b1)));
+    const int lim = min(A.W, max(j, last - j));
+    if (PAD) {
+      // Four offsets per early-exit test; the last group may read up to 3 offsets past lim,
+      // which lie inside the padding (P >= lim + 3) and, beyond W or past the row end, only
+      // give values above W^2 that the clamp maps to the same result.
+      int32_t s2 = 1;
+      for (int s = 1; s <= lim; s += 4) {
+        if (s2 >= best) break;  // every farther column is at least s^2 away
+        const int32_t q1 = s2 + 2 * s + 1, q2 = q1 + 2 * s + 3, q3 = q2 + 2 * s + 5;
+        best = min(best, s2 + min(h[j - s], h[j + s]));
+        best = min(best, q1 + min(h[j - s - 1], h[j + s + 1]));
+        best = min(best, q2 + min(h[j - s - 2], h[j + s + 2]));
+        best = min(best, q3 + min(h[j - s - 3], h[j + s + 3]));
+        s2 = q3 + 2 * s + 7;
+      }
+    } else {
+      // Offsets past a row end re-read the end column at an overstated distance (its true
+      // offset was already counted), which cannot lower the minimum: the indices are clamped.
+      for (int s = 1; s <= lim; s += 2) {
+        const int32_t s2 = s * s;
+        if (s2 >= best) break;
+        const int32_t t2 = s2 + 2 * s + 1;
+        const int32_t a0 = h[max(j - s, 0)], b0 = h[min(j + s, last)];
+        const int32_t a1 = h[max(j - s - 1, 0)], b1 = h[min(j + s + 1, last)];
+        best = min(best, min(s2 + min(a0, b0), t2 + min(a1, b1)));
+      }
     }
     float d = best > W2 ? INFINITY : A.res * sqrtf((float)best);
     d = fminf(d, A.clamp);
@@ -200,10 +243,18 @@ extern "C" int seb_risk_sdf(const seb_grid* g, float risk_obstacle, float clamp,
   A.W = (int)w;
   const cudaStream_t st = (cudaStream_t)stream;
   cols_kernel<<<dim3((unsigned)((A.nx + 31) / 32), (unsigned)A.K), kColThreads, 0, st>>>(A);
-  cudaError_t e = cudaFuncSetAttribute(rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(2 * A.nx * sizeof(int32_t)));
+  // padding of the row pass: the search reaches offset min(W, nx - 1) + 3
+  const int P = min(A.W, A.nx - 1) + 4;
+  const size_t psmem = (size_t)2 * (A.nx + 2 * (size_t)P) * sizeof(int32_t);
+  const bool pad = psmem <= kPadSmemMax;
+  const size_t rsmem = pad ? psmem : (size_t)2 * A.nx * sizeof(int32_t);
+  auto rk = pad ? rows_kernel<true> : rows_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
   if (e == cudaSuccess) {
-    rows_kernel<<<(unsigned)((int64_t)A.K * A.ny), kRowThreads, 2 * A.nx * sizeof(int32_t), st>>>(A);
+    // as few passes over the row as kRowThreads allows, split evenly between the passes
+    const int passes = (A.nx + kRowThreads - 1) / kRowThreads;
+    const int rthreads = ((A.nx + passes - 1) / passes + 31) / 32 * 32;
+    rk<<<(unsigned)((int64_t)A.K * A.ny), rthreads, rsmem, st>>>(A, P);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {
