@@ -20,6 +20,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -134,7 +135,8 @@ class Clocks:
     """nvidia-smi sampling during the timed region."""
 
     def __init__(self, index):
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        d = os.environ.get("SEB_CLOCKS_DIR", tempfile.gettempdir())
+        self.path = os.path.join(d, f"seb_clocks_rank{index}.csv")
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"

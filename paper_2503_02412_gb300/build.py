@@ -2,7 +2,7 @@
 
 Each translation unit under ``csrc/`` is compiled in parallel, then linked into
 ``paper_2503_02412_gb300/libseb.so`` (the CUDA runtime is linked statically, so the library
-only needs the driver at run time).  ``python -m paper_2503_02412_gb300.build`` runs it.
+only needs the CUDA driver at run time).  ``python -m paper_2503_02412_gb300.build`` runs it.
 """
 from __future__ import annotations
 

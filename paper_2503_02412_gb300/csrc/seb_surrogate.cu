@@ -2,8 +2,8 @@
 // elevation patch to the per-yaw (z - z_cell, pitch, roll, risk) of Algorithm 1, trained on
 // the GPU on patches the exact kernel labels, and run fully convolutionally over a map with the
 // exact kernel as fallback near unknown cells and step edges.  The paper defines no learned
-// model (it names learned traversability as less reliable, Sec. II-A); the exact kernel is the
-// judge of every prediction.
+// model (it names learned traversability as less reliable, Sec. II-A); every prediction is measured
+// against the exact kernel.
 //
 // Network (channel-last, valid convolutions): slope features (dz/dx, dz/dy by central
 // differences) -> 4 x [3x3 conv, 32 channels, dilation 1, 2, 4, 8, ReLU] -> 1x1 head to
