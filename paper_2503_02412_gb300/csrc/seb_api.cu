@@ -242,11 +242,9 @@ int seb_map_shift(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
   // keeps every surviving cell at its physical address.
   m->ring_x = (int32_t)(((m->ring_x + dx) % nx + nx) % nx);
   m->ring_y = (int32_t)(((m->ring_y + dy) % ny + ny) % ny);
-  // Bands reach the footprint's extent plus one cell block (cells of a 4 x 2 block share a
-  // reference height, so a block that straddles an edge is recomputed whole).
-  const int rx = m->T.rx + 3, ry = m->T.ry + 1;
-  // Column bands: cells that now see entering columns, and cells that used to see columns
-  // that left the window.
+  // Column bands: cells that now see entering columns, and cells that used to see columns that
+  // left the window (the footprint's reach inwards from either edge).  Row bands likewise.
+  const int rx = m->T.rx, ry = m->T.ry;
   int left = 0, right = 0, top = 0, bottom = 0;
   if (dx > 0) {
     right = (int)dx + rx;
@@ -262,6 +260,14 @@ int seb_map_shift(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
     top = (int)(-dy) + ry;
     bottom = ry;
   }
+  // Cells of a 4 x 2 block (world column = 0 mod 4, world row = 0 mod 2) share a reference
+  // height, so each band is widened to whole blocks: a block with a cell in a band is
+  // recomputed whole, and every other block keeps its inputs and its reference.
+  const int px = (int)(((oi % 4) + 4) % 4), py = (int)(((oj % 2) + 2) % 2);
+  if (left > 0) left += (4 - (left + px) % 4) % 4;
+  if (right > 0) right += (nx - right + px) % 4;
+  if (top > 0) top += (2 - (top + py) % 2) % 2;
+  if (bottom > 0) bottom += (ny - bottom + py) % 2;
   Launch L = base_launch(m, elev);
   launch_set_origin(L, oi, oj);
   if (left + right >= nx || top + bottom >= ny) {
