@@ -140,6 +140,17 @@ def test_parameter_variants(seb, extra):
     check(out, fl, oracle_grid(cfg, e), str(extra))
 
 
+def test_large_footprint_per_cell_kernel(seb):
+    """A 4.0 x 3.0 m footprint at 0.05 m (reach 50 cells, ~4,800 points per cell): the sliding
+    kernel's staged tile for the 16-column layout would need more than 227 KB of shared memory,
+    so the launch runs the per-cell kernel in plain FP32."""
+    cfg = dict(nx=120, ny=96, n_yaw=4, res=0.05, length=4.0, width=3.0)
+    e = fractal_steps_nan(21, 120, 96, nan_frac=0.02)
+    _, out, fl, _ = run_map(seb, cfg, e, n_min=100)
+    s = check(out, fl, oracle_grid(cfg, e, n_min=100), "large footprint")
+    assert s["assessed"] > 0.5 * s["n"]
+
+
 def test_rolling_window_bit_identical_to_rebuild(seb):
     """Sec. V-A: the window follows the robot; after 50 moves of 10 cells in random
     directions the ring-buffered map equals a fresh rebuild of the final window, bit for bit,
