@@ -206,9 +206,17 @@ __global__ void __launch_bounds__(128) conv_fwd_kernel(const bf16* __restrict__ 
         for (int o = 0; o < kHid; ++o) acc[o] = fmaf(xv, wr[o], acc[o]);
       }
     }
-    bf16* yp = y + p * kHid;
+    // 16-byte stores: the 32 outputs of a pixel are 64 contiguous bytes
+    uint4* yp = reinterpret_cast<uint4*>(y + p * kHid);
 #pragma unroll
-    for (int o = 0; o < kHid; ++o) yp[o] = __float2bfloat16_rn(fmaxf(acc[o], 0.f));
+    for (int q = 0; q < kHid / 8; ++q) {
+      uint4 v;
+      __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(&v);
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        h2[t] = __floats2bfloat162_rn(fmaxf(acc[8 * q + 2 * t], 0.f), fmaxf(acc[8 * q + 2 * t + 1], 0.f));
+      yp[q] = v;
+    }
   }
 }
 
@@ -497,8 +505,10 @@ __global__ void init_kernel(float* __restrict__ p, float* __restrict__ m, float*
 constexpr int kTcM = 128;
 constexpr int kTcK = 9 * kHid;                      // 288
 constexpr int kTcKCores = kTcK / 8;                  // 36
-constexpr int kTcBOff = 80 * 1024;                   // B after A, 1 KB aligned
-constexpr int kTcSmem = 128 * 1024 + 256;            // room for any stride reading, + barrier
+constexpr int kTcBOff = 72 * 1024;                   // B right after A (128 x 288 BF16), 1 KB aligned
+constexpr int kTcBarOff = kTcBOff + 18 * 1024;       // after B (32 x 288 BF16)
+constexpr int kTcSmem = kTcBarOff + 256;             // + barrier: two CTAs fit on an SM
+static_assert(kTcBOff >= kTcM * kTcK * 2 && kTcBarOff >= kTcBOff + kHid * kTcK * 2, "operand regions overlap");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -521,40 +531,49 @@ __device__ __forceinline__ uint32_t tc_off(int row, int k, int nrow_cores) {
 }
 
 template <bool RELU>
-__global__ void __launch_bounds__(kTcM, 1) conv_tc_kernel(const bf16* __restrict__ x, const bf16* __restrict__ w,
+__global__ void __launch_bounds__(kTcM, 2) conv_tc_kernel(const bf16* __restrict__ x, const bf16* __restrict__ w,
                                                           const float* __restrict__ bias, int B, int H, int W, int d,
                                                           bf16* __restrict__ y, uint32_t* err) {
   extern __shared__ __align__(1024) uint8_t tsm[];
   uint8_t* As = tsm;
   uint8_t* Bs = tsm + kTcBOff;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(tsm + 128 * 1024);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(tsm + 128 * 1024 + 16);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(tsm + kTcBarOff);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tsm + kTcBarOff + 16);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int Ho = H - 2 * d, Wo = W - 2 * d;
   const int64_t P = (int64_t)B * Ho * Wo;
   const int64_t p = (int64_t)blockIdx.x * kTcM + tid;
 
-  // B: weights [co][tap][ci] -> K-major rows co, k = tap * 32 + ci (16 bytes per store)
+  // Operands are copied global -> shared with cp.async (16 bytes each, all in flight at once).
+  auto cp16 = [](uint8_t* dst, const void* src, uint32_t bytes) {  // bytes < 16: zero fill
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(bytes)
+                 : "memory");
+  };
+  // B: weights [co][tap][ci] -> K-major rows co, k = tap * 32 + ci
   for (int i = tid; i < kHid * kTcKCores; i += kTcM) {
     const int co = i / kTcKCores, kc = i - co * kTcKCores;
-    const uint4 v = *reinterpret_cast<const uint4*>(w + (int64_t)co * kTcK + kc * 8);
-    *reinterpret_cast<uint4*>(Bs + tc_off(co, kc * 8, kHid / 8)) = v;
+    cp16(Bs + tc_off(co, kc * 8, kHid / 8), w + (int64_t)co * kTcK + kc * 8, 16u);
   }
-  // A: this thread's im2col row
-  if (p < P) {
-    const int b = (int)(p / ((int64_t)Ho * Wo));
-    const int rem = (int)(p - (int64_t)b * Ho * Wo);
-    const int i = rem / Wo, j = rem - i * Wo;
+  // A: this thread's im2col row (zeros past the last pixel)
+  {
+    int b = 0, i = 0, j = 0;
+    const uint32_t bytes = p < P ? 16u : 0u;
+    if (p < P) {
+      b = (int)(p / ((int64_t)Ho * Wo));
+      const int rem = (int)(p - (int64_t)b * Ho * Wo);
+      i = rem / Wo;
+      j = rem - i * Wo;
+    }
+#pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
       const int u = tap / 3, v = tap - u * 3;
-      const uint4* src = reinterpret_cast<const uint4*>(x + (((int64_t)b * H + i + u * d) * W + j + v * d) * kHid);
+      const bf16* src = x + (((int64_t)b * H + i + u * d) * W + j + v * d) * kHid;
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        *reinterpret_cast<uint4*>(As + tc_off(tid, tap * kHid + q * 8, kTcM / 8)) = src[q];
+      for (int q = 0; q < 4; ++q) cp16(As + tc_off(tid, tap * kHid + q * 8, kTcM / 8), src + q * 8, bytes);
     }
-  } else {
-    for (int kc = 0; kc < kTcKCores; ++kc) *reinterpret_cast<uint4*>(As + tc_off(tid, kc * 8, kTcM / 8)) = make_uint4(0, 0, 0, 0);
   }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)), "r"(32));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -606,15 +625,23 @@ __global__ void __launch_bounds__(kTcM, 1) conv_tc_kernel(const bf16* __restrict
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     if (p < P) {
-      bf16* yp = y + p * kHid;
+      // 16-byte stores: the 32 outputs of a pixel are 64 contiguous bytes
+      uint4* yp = reinterpret_cast<uint4*>(y + p * kHid);
 #pragma unroll
-      for (int o = 0; o < kHid; o += 2) {
-        float v0 = __uint_as_float(r[o]) + bias[o], v1 = __uint_as_float(r[o + 1]) + bias[o + 1];
-        if (RELU) {
-          v0 = fmaxf(v0, 0.f);
-          v1 = fmaxf(v1, 0.f);
+      for (int q = 0; q < kHid / 8; ++q) {
+        uint4 v;
+        __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(&v);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int o = 8 * q + 2 * t;
+          float v0 = __uint_as_float(r[o]) + bias[o], v1 = __uint_as_float(r[o + 1]) + bias[o + 1];
+          if (RELU) {
+            v0 = fmaxf(v0, 0.f);
+            v1 = fmaxf(v1, 0.f);
+          }
+          h2[t] = __floats2bfloat162_rn(v0, v1);
         }
-        *reinterpret_cast<__nv_bfloat162*>(yp + o) = __floats2bfloat162_rn(v0, v1);
+        yp[q] = v;
       }
     }
   }
@@ -724,6 +751,61 @@ __global__ void mask_kernel(const float* __restrict__ elev, int nx, int ny, floa
     mask[i] = m ? 1 : 0;
     if (m) tile_active[(r / 32) * tiles_x + c / 32] = 1;
   }
+}
+
+// The same mask by 32 x 32 tiles (radius <= kMaskMaxR): per cell of the tile and its halo the
+// source flag (unknown, or a step to the right or below), then the Chebyshev dilation as a
+// row pass and a column pass in shared memory.
+constexpr int kMaskTile = 32, kMaskMaxR = 8, kMaskExt = kMaskTile + 2 * kMaskMaxR;
+__global__ void __launch_bounds__(256) mask_tiled_kernel(const float* __restrict__ elev, int nx, int ny, float step,
+                                                         int radius, uint8_t* __restrict__ mask,
+                                                         uint8_t* __restrict__ tile_active, int tiles_x) {
+  __shared__ uint8_t src[kMaskExt][kMaskExt];
+  __shared__ uint8_t hor[kMaskExt][kMaskTile];
+  __shared__ int any;
+  const int R = radius, E = kMaskTile + 2 * R;
+  const int r0 = blockIdx.y * kMaskTile, c0 = blockIdx.x * kMaskTile;
+  if (threadIdx.x == 0) any = 0;
+  for (int t = threadIdx.x; t < E * E; t += blockDim.x) {
+    const int i = t / E, j = t - i * E;
+    const int rr = r0 - R + i, cc = c0 - R + j;
+    uint8_t f = 0;
+    if (rr >= 0 && rr < ny && cc >= 0 && cc < nx) {
+      const float z = elev[(int64_t)rr * nx + cc];
+      if (z != z) {
+        f = 1;
+      } else {
+        if (cc + 1 < nx) {
+          const float zr = elev[(int64_t)rr * nx + cc + 1];
+          if (zr == zr && fabsf(zr - z) > step) f = 1;
+        }
+        if (rr + 1 < ny) {
+          const float zd = elev[(int64_t)(rr + 1) * nx + cc];
+          if (zd == zd && fabsf(zd - z) > step) f = 1;
+        }
+      }
+    }
+    src[i][j] = f;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < E * kMaskTile; t += blockDim.x) {
+    const int i = t / kMaskTile, j = t - i * kMaskTile;
+    uint8_t h = 0;
+    for (int k = 0; k <= 2 * R; ++k) h |= src[i][j + k];
+    hor[i][j] = h;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < kMaskTile * kMaskTile; t += blockDim.x) {
+    const int i = t / kMaskTile, j = t - i * kMaskTile;
+    const int r = r0 + i, c = c0 + j;
+    if (r >= ny || c >= nx) continue;
+    uint8_t m = r < kMargin || c < kMargin || r >= ny - kMargin || c >= nx - kMargin;
+    for (int k = 0; k <= 2 * R; ++k) m |= hor[i + k][j];
+    mask[(int64_t)r * nx + c] = m;
+    if (m) any = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && any) tile_active[blockIdx.y * tiles_x + blockIdx.x] = 1;
 }
 
 int grid_for(int64_t n, int threads) {
@@ -1081,7 +1163,10 @@ int seb_sur_infer(seb_sur* h, const float* elev, float step, int32_t radius, int
   const int tx = (nx + 31) / 32, ty = (ny + 31) / 32;
   int rc = cuda_check(cudaMemsetAsync(tiles, 0, (size_t)tx * ty, st), "tile flags");
   if (rc) return rc;
-  mask_kernel<<<grid_for((int64_t)nx * ny, 256), 256, 0, st>>>(elev, nx, ny, step, radius, mask, tiles, tx);
+  if (radius >= 0 && radius <= kMaskMaxR)
+    mask_tiled_kernel<<<dim3((unsigned)tx, (unsigned)ty), 256, 0, st>>>(elev, nx, ny, step, radius, mask, tiles, tx);
+  else
+    mask_kernel<<<grid_for((int64_t)nx * ny, 256), 256, 0, st>>>(elev, nx, ny, step, radius, mask, tiles, tx);
   rc = cuda_check(cudaGetLastError(), "surrogate inference");
   if (rc || !exact_fallback) return rc;
   seb::Launch L;

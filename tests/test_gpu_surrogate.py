@@ -168,6 +168,31 @@ def test_exact_fallback_cells(mods):
     assert ((ff[:, ~sel] & seb.abi.SEB_FLAG_SURROGATE) != 0).all()
 
 
+@pytest.mark.parametrize("radius", [0, 3, 8, 10])
+def test_fallback_mask_definition(mods, radius):
+    """The fallback mask is the Chebyshev dilation (radius) of the source cells, those that are
+    unknown or whose right or lower neighbour is known and differs by more than the step, plus
+    the network's 16-cell margin; compared on every cell of a map with NaN discs and steps."""
+    seb, _ = mods
+    s = make(mods, nx=160, batch=1, seed=9)
+    e = fractal_steps_nan(5, 160, 160, nan_frac=0.03)
+    step = np.float32(0.04)
+    _, _, mask = s.infer(torch.from_numpy(e).cuda(), step=float(step), radius=radius, exact_fallback=False)
+    nan = np.isnan(e)
+    src = nan.copy()
+    with np.errstate(invalid="ignore"):
+        src[:, :-1] |= ~nan[:, :-1] & ~nan[:, 1:] & (np.abs(e[:, 1:] - e[:, :-1]) > step)
+        src[:-1, :] |= ~nan[:-1, :] & ~nan[1:, :] & (np.abs(e[1:, :] - e[:-1, :]) > step)
+    pad = np.pad(src, radius)
+    dil = np.zeros_like(src)
+    for dr in range(2 * radius + 1):
+        for dc in range(2 * radius + 1):
+            dil |= pad[dr:dr + 160, dc:dc + 160]
+    dil[:16] = dil[-16:] = True
+    dil[:, :16] = dil[:, -16:] = True
+    assert np.array_equal(mask.cpu().numpy().astype(bool), dil)
+
+
 def test_training_gain_report(mods, record_property):
     """Trains on bumpy-plane patches labelled by the exact kernel, then compares the network
     with the exact kernel on held-out maps: error on the cells it predicts, fallback share,
