@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--sur-patches", type=int, default=200_000, help="surrogate training patches")
     ap.add_argument("--profile-cycle", action="store_true",
                     help="run only the local-mapping cycle row (the program profiled for its launch list)")
+    ap.add_argument("--profile-surrogate", action="store_true",
+                    help="run five surrogate inferences (with the exact fallback) of the 400x400x72 map only")
     ap.add_argument("--profile-rebuild", action="store_true",
                     help="only run three full rebuilds of the map (a short program for ncu)")
     return ap.parse_args()
@@ -237,6 +239,24 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def profile_surrogate():
+    """Five surrogate inferences of the 400x400x72 fractal map with the exact fallback (weights
+    from the seeded initialisation: the timing does not depend on them)."""
+    import torch
+
+    import paper_2503_02412_gb300 as seb
+    from paper_2503_02412_gb300 import surrogate
+    from synthetic import fractal_steps_nan
+
+    s = surrogate.Surrogate(seb.SebParams(nx=NX, ny=NY, n_yaw=K, res=RES, length=LENGTH, width=WIDTH), max_batch=256)
+    s.init(11)
+    e = torch.from_numpy(fractal_steps_nan(13)).cuda()
+    out, fl, mask = s.infer(e)
+    for _ in range(4):
+        s.infer_into(e, out, fl, mask)
+    torch.cuda.synchronize()
+
+
 def profile_rebuild():
     """Three rebuilds of the 400x400x72 map and nothing else: the program ncu captures."""
     import torch
@@ -256,6 +276,8 @@ def main():
     args = parse()
     if args.profile_rebuild:
         return profile_rebuild()
+    if args.profile_surrogate:
+        return profile_surrogate()
     if args.profile_cycle:
         import torch
 
