@@ -37,6 +37,7 @@ CYCLE_SIDE, CYCLE_RES, CYCLE_YAWS = 180, 0.1, 30
 N_SHIFTS = 50
 WORLD = 1200
 WORKLOAD = "se2_map_400x400x72_rebuild_plus_50_shifts"
+METRIC = "SE(2) cells/s (400x400x72 map: full rebuild + 50 rolling shifts per step)"
 
 # ncu DRAM traffic of one full-map rebuild launch (dram__bytes_read.sum + dram__bytes_write.sum),
 # valid only for the kernel source it was captured on (hash of the assess kernel's sources).
@@ -228,7 +229,7 @@ def run_reference(args):
         oracle.assess_cells(p, e, cells, o, n_threads=cb["cores"])
     dt = time.perf_counter() - t0
     value = n * args.steps / dt
-    line = {"impl": "reference", "metric": "SE(2) cells/s (400x400x72 map, rebuild + rolling shifts)",
+    line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": "SE(2) cells/s", "n_gpus": world_size, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -369,7 +370,7 @@ def main():
         e2e = run_e2e(seb, m, world_np, origins, args, dev)
     rows = None if args.no_rows or world_size > 1 else measure_rows(seb, args, dev)
     line = {
-        "metric": "SE(2) cells/s (400x400x72 map: full rebuild + 50 rolling shifts per step)",
+        "metric": METRIC,
         "value": value, "unit": "SE(2) cells/s", "n_gpus": world_size, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
