@@ -4,9 +4,11 @@ TEST INFRASTRUCTURE ONLY (like the rest of ``oracle/``): the GPU tests compare l
 surrogate kernels with these functions on the same inputs.  The paper defines no learned
 model (it notes learned traversability as unreliable, Sec. II-A); what is fixed here is plain
 mathematics: valid dilated cross-correlation, ReLU, a 1x1 head, mean squared error, its exact
-gradient, and Adam (Kingma & Ba, 2015).  Pins: ``tests/test_surrogate_pins.py`` (against
-scipy.signal.correlate and central differences).  The network itself has no paper pin:
-parity unpinned beyond these definitions.
+gradient, and Adam (Kingma & Ba, 2015).  Pins: ``tests/test_surrogate_pins.py`` (BF16 rounding,
+the convolution against scipy.signal.correlate, the features and the network gradient against
+central differences, the first Adam step against its closed form).  The network is not the
+paper's, so no value printed in the paper applies to it; every function here is pinned by
+the mathematics above.
 
 Tensors are channel-last: activations [B][H][W][C], conv weights [Cout][3][3][Cin], head
 weights [Cout][Cin].  Stored activations and weights are rounded to bfloat16 (round to
