@@ -112,6 +112,37 @@ def test_degenerate_calls(seb):
         seb.SE2Grid.from_map(m, 4)
 
 
+def test_max_yaw_bins(seb):
+    """The interface limits: 4096 yaw bins with yaws up to |1e4| rad (the yaw reduction stays
+    exact there), against the FP64 reference; 4097 bins are rejected."""
+    K2, ny, nx = 4096, 6, 7
+    grid = random_se2_grid(31, K2, ny, nx)
+    rng = np.random.default_rng(32)
+    n = 50_000
+    P = np.stack([(ORIGIN[0] + rng.uniform(0, nx - 1, n) + 0.5) * RES, (ORIGIN[1] + rng.uniform(0, ny - 1, n) + 0.5) * RES,
+                  rng.uniform(-1e4, 1e4, n)], 1).astype(np.float32)
+    ring = (3, 2)
+    g = seb.SE2Grid.from_tensor(torch.from_numpy(grid).cuda(), RES, ORIGIN, ring)
+    val, grad, fl = seb.se2_lookup(g, torch.from_numpy(P).cuda(), fill=0.0, with_grad=True)
+    rv, rg, rf = ref_lookup(grid.astype(np.float64), P.astype(np.float64), RES_F, ORIGIN, ring, 0.0)
+    val, grad, fl = val.cpu().numpy(), grad.cpu().numpy(), fl.cpu().numpy()
+    assert np.array_equal(fl, rf) and (rf == 0).mean() > 0.99
+    assert np.abs(val - rv).max() <= VAL_TOL
+    Pd = P.astype(np.float64)
+    q = [Pd[:, 0] / RES_F - ORIGIN[0] - 0.5, Pd[:, 1] / RES_F - ORIGIN[1] - 0.5, Pd[:, 2] * K2 / (2 * math.pi)]
+    ok = np.ones(n, bool)
+    for c in q:
+        f = c - np.floor(c)
+        ok &= (f > 1e-4) & (f < 1 - 1e-4)
+    # a derivative in grid units carries ~1e-6 (a few ulps of the O(1) values); in world units it
+    # scales by 1 / res for x, y and by K / (2 pi) = 652 for the yaw
+    scale = np.array([1 / RES_F, 1 / RES_F, K2 / (2 * math.pi)])
+    assert (np.abs(grad[ok] - rg[ok]) <= 1e-5 * scale + GRAD_RTOL * np.abs(rg[ok])).all()
+    with pytest.raises(seb.abi.SebError):
+        bad = seb.SE2Grid.from_tensor(torch.zeros((4097, 2, 2), device="cuda"), RES)
+        seb.se2_lookup(bad, torch.zeros((3, 3), device="cuda"))
+
+
 def test_map_channel_vs_exact_query(seb):
     """On a tilted plane the bilinear z is exact and pitch/roll differ from the exact continuous
     query by the yaw discretisation only: |error| <= (2 pi / K)^2 / 8 * max |d^2/dyaw^2|,

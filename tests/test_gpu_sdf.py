@@ -75,6 +75,22 @@ def test_map_sized_grid_sampled(seb):
     assert np.abs(g - ref).max() <= TOL * 2.0
 
 
+def test_long_rows_clamped_search(seb):
+    """Rows whose sentinel padding would exceed the row pass's shared-memory budget (6000
+    columns, a 160 m clamp: W = 3201 cells) take the clamped two-offset search; sampled cells
+    against the FP64 reference, with sparse obstacles so that the searches run long."""
+    K, ny, nx = 2, 3, 6000
+    risk = obstacle_risk(41, K, ny, nx, n_blobs=3, blob_cells=(1, 2))
+    got = gpu_sdf(seb, risk, ring=(1234, 1), clamp=160.0)._owner.cpu().numpy()
+    rng = np.random.default_rng(42)
+    m = 1500
+    cells = np.stack([rng.integers(0, nx, m), rng.integers(0, ny, m), rng.integers(0, K, m)], 1)
+    ref = ref_sdf(risk.astype(np.float64), RES_F, clamp=160.0, ring=(1234, 1), cells=cells)
+    g = got[cells[:, 2], (cells[:, 1] + 1) % ny, (cells[:, 0] + 1234) % nx]
+    assert np.abs(ref).max() > 20.0  # long searches, not the clamp
+    assert np.abs(g - ref).max() <= TOL * 160.0
+
+
 def test_sdf_grid_lookup(seb):
     """The SDF comes back as a grid the trilinear lookup reads directly."""
     risk = obstacle_risk(11, 8, 30, 40)
