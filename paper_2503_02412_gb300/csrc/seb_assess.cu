@@ -424,6 +424,10 @@ __global__ void __launch_bounds__(kThreads, 2)
   int* rowflag = reinterpret_cast<int*>(smem);
   float2* qs = reinterpret_cast<float2*>(smem + kMaxStageRows);  // [kSlQ][kThreads]
   float2* pt = qs + kSlQ * kThreads;                             // [sh - 1][sw2] vertical pairs
+  // Programmatic launch: this grid's CTAs may be scheduled while the previous kernel of the
+  // stream drains, but nothing reads or writes global memory before that kernel has completed.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
   if (blockDim.x != kThreads || blockIdx.y >= (unsigned)T.n_pairs) {
     if (threadIdx.x == 0) atomicOr(L.err, kErrLaunchShape);
     return;
@@ -811,9 +815,18 @@ cudaError_t launch_typed(const Tables& T, const Launch& Lreq, cudaStream_t strea
       auto kern = assess_kernel_sl<E>;
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      const dim3 grid(L.tile_start[L.n_rects], T.n_pairs);
-      kern<<<grid, kThreads, smem, stream>>>(T, L);
-      return cudaGetLastError();
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(L.tile_start[L.n_rects], T.n_pairs);
+      cfg.blockDim = dim3(kThreads);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = stream;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      e = cudaLaunchKernelEx(&cfg, kern, T, L);
+      return e != cudaSuccess ? e : cudaGetLastError();
     }
     // very large footprints: the per-cell kernel below
   }
