@@ -424,10 +424,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   int* rowflag = reinterpret_cast<int*>(smem);
   float2* qs = reinterpret_cast<float2*>(smem + kMaxStageRows);  // [kSlQ][kThreads]
   float2* pt = qs + kSlQ * kThreads;                             // [sh - 1][sw2] vertical pairs
-  // Programmatic launch: this grid's CTAs may be scheduled while the previous kernel of the
-  // stream drains, but nothing reads or writes global memory before that kernel has completed.
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;");
+  pdl_entry();  // no global memory access before the stream's previous kernel has completed
   if (blockDim.x != kThreads || blockIdx.y >= (unsigned)T.n_pairs) {
     if (threadIdx.x == 0) atomicOr(L.err, kErrLaunchShape);
     return;
@@ -714,6 +711,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 }
 
 __global__ void copy_out_kernel(const Launch L, float* __restrict__ dst, uint8_t* __restrict__ fdst) {
+  seb::pdl_entry();
   const int64_t total = (int64_t)L.n_yaw * L.plane;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -815,18 +813,7 @@ cudaError_t launch_typed(const Tables& T, const Launch& Lreq, cudaStream_t strea
       auto kern = assess_kernel_sl<E>;
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(L.tile_start[L.n_rects], T.n_pairs);
-      cfg.blockDim = dim3(kThreads);
-      cfg.dynamicSmemBytes = smem;
-      cfg.stream = stream;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-      attr[0].val.programmaticStreamSerializationAllowed = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      e = cudaLaunchKernelEx(&cfg, kern, T, L);
-      return e != cudaSuccess ? e : cudaGetLastError();
+      return launch_pdl(kern, dim3(L.tile_start[L.n_rects], T.n_pairs), dim3(kThreads), smem, stream, T, L);
     }
     // very large footprints: the per-cell kernel below
   }
@@ -869,8 +856,7 @@ cudaError_t launch_copy_out(const Launch& L, float* out_dev, uint8_t* flags_dev,
   int blocks = (int)((total + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
-  copy_out_kernel<<<blocks, 256, 0, stream>>>(L, out_dev, flags_dev);
-  return cudaGetLastError();
+  return launch_pdl(copy_out_kernel, dim3(blocks), dim3(256), 0, stream, L, out_dev, flags_dev);
 }
 
 }  // namespace seb

@@ -79,6 +79,7 @@ __device__ __forceinline__ int64_t store_idx(const ElevArgs& A, int64_t wi, int6
 }
 
 __global__ void move_kernel(ElevArgs A, float* h, float* s2) {
+  seb::pdl_entry();
   const int64_t n = (int64_t)A.nx * A.ny;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(t / A.nx), c = (int)(t - (int64_t)r * A.nx);
@@ -96,6 +97,7 @@ __global__ void move_kernel(ElevArgs A, float* h, float* s2) {
 __global__ void points_kernel(ElevArgs A, const float* __restrict__ pts, int64_t n, int32_t* __restrict__ cell,
                               double* __restrict__ pz, uint8_t* __restrict__ inside, double* __restrict__ pw,
                               double* __restrict__ rinv) {
+  seb::pdl_entry();
   double JS[3], RtB[3];
   {
     // J_S = (R_B R_BS)^T b3: the third row of R_B R_BS; R_B^T b3: the third row of R_B
@@ -148,6 +150,7 @@ constexpr int kRaySegs = 8;
 
 __global__ void raycast_kernel(ElevArgs A, const double* __restrict__ pw, const double* __restrict__ rinv,
                                const uint8_t* __restrict__ inside, int64_t n, float* h, float* s2) {
+  seb::pdl_entry();
   const double sx = A.sx * A.inv_res, sy = A.sy * A.inv_res, sz = A.sz;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * kRaySegs;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -218,6 +221,7 @@ __global__ void raycast_kernel(ElevArgs A, const double* __restrict__ pw, const 
 __global__ void accumulate_kernel(ElevArgs A, const int32_t* __restrict__ cell, const double* __restrict__ pz,
                                   int64_t n, const float* __restrict__ h, const float* __restrict__ s2,
                                   double* __restrict__ acc, int32_t* __restrict__ nup) {
+  seb::pdl_entry();
   const int64_t plane = (int64_t)A.nx * A.ny;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t c = cell[i];
@@ -237,6 +241,7 @@ __global__ void accumulate_kernel(ElevArgs A, const int32_t* __restrict__ cell, 
 }
 
 __global__ void finalize_kernel(int64_t plane, float* h, float* s2, double* acc, int32_t* nup) {
+  seb::pdl_entry();
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < plane; c += (int64_t)gridDim.x * blockDim.x) {
     const double aw = acc[c], awz = acc[plane + c], uw = acc[2 * plane + c], uwz = acc[3 * plane + c];
     const int up = nup[c];
@@ -259,6 +264,7 @@ __global__ void finalize_kernel(int64_t plane, float* h, float* s2, double* acc,
 }
 
 __global__ void copy_out_kernel(ElevArgs A, const float* h, const float* s2, float* ho, float* so) {
+  seb::pdl_entry();
   const int64_t n = (int64_t)A.nx * A.ny;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(t / A.nx), c = (int)(t - (int64_t)r * A.nx);
@@ -441,14 +447,19 @@ int seb_elev_integrate(seb_elev* e, const seb_scan_pose* pose, const float* pts,
   A.sz = sw[2];
   const cudaStream_t st = e->stream;
   const int64_t plane = (int64_t)e->p.nx * e->p.ny;
-  move_kernel<<<blocks_for(plane), 256, 0, st>>>(A, e->h, e->s2);
-  if (n > 0) {
-    points_kernel<<<blocks_for(n), 256, 0, st>>>(A, pts, n, e->cell, e->pz, e->inside, e->pw, e->rinv);
-    raycast_kernel<<<blocks_for(n * kRaySegs), 256, 0, st>>>(A, e->pw, e->rinv, e->inside, n, e->h, e->s2);
-    accumulate_kernel<<<blocks_for(n), 256, 0, st>>>(A, e->cell, e->pz, n, e->h, e->s2, e->acc, e->nup);
-    finalize_kernel<<<blocks_for(plane), 256, 0, st>>>(plane, e->h, e->s2, e->acc, e->nup);
-  }
-  const cudaError_t err = cudaGetLastError();
+  cudaError_t err = seb::launch_pdl(move_kernel, dim3(blocks_for(plane)), dim3(256), 0, st, A, e->h, e->s2);
+  if (n > 0 && err == cudaSuccess)
+    err = seb::launch_pdl(points_kernel, dim3(blocks_for(n)), dim3(256), 0, st, A, pts, n, e->cell, e->pz, e->inside,
+                          e->pw, e->rinv);
+  if (n > 0 && err == cudaSuccess)
+    err = seb::launch_pdl(raycast_kernel, dim3(blocks_for(n * kRaySegs)), dim3(256), 0, st, A, e->pw, e->rinv,
+                          e->inside, n, e->h, e->s2);
+  if (n > 0 && err == cudaSuccess)
+    err = seb::launch_pdl(accumulate_kernel, dim3(blocks_for(n)), dim3(256), 0, st, A, e->cell, e->pz, n, e->h, e->s2,
+                          e->acc, e->nup);
+  if (n > 0 && err == cudaSuccess)
+    err = seb::launch_pdl(finalize_kernel, dim3(blocks_for(plane)), dim3(256), 0, st, plane, e->h, e->s2, e->acc,
+                          e->nup);
   if (err != cudaSuccess) {
     seb::set_error("seb_elev_integrate launch: %s", cudaGetErrorString(err));
     return SEB_ERR_CUDA;
@@ -473,8 +484,9 @@ int seb_elev_view_get(const seb_elev* e, seb_elev_view* v) {
 int seb_elev_copy_out(const seb_elev* e, float* height, float* variance) {
   if (!e) return fail(SEB_ERR_INVALID_ARG, "seb_elev_copy_out: NULL");
   ElevArgs A = args_of(e, nullptr);
-  copy_out_kernel<<<blocks_for((int64_t)e->p.nx * e->p.ny), 256, 0, e->stream>>>(A, e->h, e->s2, height, variance);
-  const cudaError_t err = cudaGetLastError();
+  const cudaError_t lerr = seb::launch_pdl(copy_out_kernel, dim3(blocks_for((int64_t)e->p.nx * e->p.ny)), dim3(256), 0,
+                                           e->stream, A, e->h, e->s2, height, variance);
+  const cudaError_t err = lerr != cudaSuccess ? lerr : cudaGetLastError();
   if (err != cudaSuccess) {
     seb::set_error("seb_elev_copy_out launch: %s", cudaGetErrorString(err));
     return SEB_ERR_CUDA;

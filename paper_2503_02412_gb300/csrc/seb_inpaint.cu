@@ -31,6 +31,7 @@ constexpr int32_t kFar = 1 << 30;  // no known cell: above any squared distance 
 
 __global__ void __launch_bounds__(kColThreads) nn_cols_kernel(const float* __restrict__ elev, int nx, int ny,
                                                               int32_t* __restrict__ near_row) {
+  seb::pdl_entry();
   __shared__ int seg_rows[kSegs][2][32];  // last known row, first known row of each segment
   const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
   const int j = blockIdx.x * 32 + lane;
@@ -69,6 +70,7 @@ __global__ void __launch_bounds__(kRowThreads) nn_rows_kernel(const float* __res
                                                               const int32_t* __restrict__ near_row, int nx,
                                                               int ny, int W, float* __restrict__ out,
                                                               int32_t* __restrict__ src) {
+  seb::pdl_entry();
   extern __shared__ int32_t h[];  // [nx]: squared row distance to column j's nearest known cell
   const int i = blockIdx.x;
   const int32_t* nr = near_row + (int64_t)i * nx;
@@ -153,13 +155,13 @@ extern "C" int seb_inpaint_nearest(const float* elev, int32_t nx, int32_t ny, in
   const int W = max_cells > 0 && max_cells < kMaxSide ? max_cells : 0;  // 0: unbounded
   int32_t* near_row = static_cast<int32_t*>(work);
   const cudaStream_t st = (cudaStream_t)stream;
-  nn_cols_kernel<<<(unsigned)((nx + 31) / 32), kColThreads, 0, st>>>(elev, nx, ny, near_row);
-  cudaError_t e = cudaFuncSetAttribute(nn_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(nx * sizeof(int32_t)));
-  if (e == cudaSuccess) {
-    nn_rows_kernel<<<(unsigned)ny, kRowThreads, nx * sizeof(int32_t), st>>>(elev, near_row, nx, ny, W, out, src);
-    e = cudaGetLastError();
-  }
+  cudaError_t e =
+      seb::launch_pdl(nn_cols_kernel, dim3((unsigned)((nx + 31) / 32)), dim3(kColThreads), 0, st, elev, nx, ny, near_row);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(nn_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(nx * sizeof(int32_t)));
+  if (e == cudaSuccess)
+    e = seb::launch_pdl(nn_rows_kernel, dim3((unsigned)ny), dim3(kRowThreads), nx * sizeof(int32_t), st, elev, near_row, nx,
+                        ny, W, out, src);
   if (e != cudaSuccess) {
     seb::set_error("seb_inpaint_nearest launch: %s", cudaGetErrorString(e));
     return SEB_ERR_CUDA;

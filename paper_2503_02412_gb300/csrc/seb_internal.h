@@ -127,4 +127,32 @@ void launch_set_origin(Launch& L, int64_t origin_i, int64_t origin_j);
 
 void set_error(const char* fmt, ...);
 
+#ifdef __CUDACC__
+// Programmatic dependent launch.  A kernel launched with launch_pdl may be scheduled while the
+// stream's previous kernel drains; it calls pdl_entry() before any global memory access, which
+// waits until that kernel has completed and its writes are visible (for an ordinary launch it
+// returns at once), and lets the next such kernel be scheduled in turn.
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+#endif
+
 }  // namespace seb

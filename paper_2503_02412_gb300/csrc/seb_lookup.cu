@@ -147,6 +147,7 @@ __device__ __forceinline__ Blend blend(const LookupArgs& A, int c0, int r0, int 
 __global__ void __launch_bounds__(256) lookup_kernel(const LookupArgs A, const float* __restrict__ poses, int64_t n,
                                                      float* __restrict__ val, float* __restrict__ grad,
                                                      uint8_t* __restrict__ flags) {
+  seb::pdl_entry();
   const float yaw_unit = A.yaw_unit;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int c0, r0, k0, k1;
@@ -174,6 +175,7 @@ __global__ void __launch_bounds__(256) lookup_kernel(const LookupArgs A, const f
 __global__ void __launch_bounds__(256) lookup_vjp_kernel(const LookupArgs A, const float* __restrict__ poses,
                                                          int64_t n, const float* __restrict__ gval,
                                                          float* __restrict__ gpose) {
+  seb::pdl_entry();
   const float yaw_unit = A.yaw_unit;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int c0, r0, k0, k1;
@@ -245,8 +247,8 @@ extern "C" int seb_se2_lookup(const seb_grid* g, const float* poses, int64_t n, 
     return SEB_ERR_INVALID_ARG;
   }
   if (n == 0) return SEB_OK;
-  lookup_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(args_of(g, fill), poses, n, val, grad, flags);
-  const cudaError_t e = cudaGetLastError();
+  const cudaError_t e = seb::launch_pdl(lookup_kernel, dim3(blocks_for(n)), dim3(256), 0, (cudaStream_t)stream,
+                                        args_of(g, fill), poses, n, val, grad, flags);
   if (e != cudaSuccess) {
     seb::set_error("seb_se2_lookup launch: %s", cudaGetErrorString(e));
     return SEB_ERR_CUDA;
@@ -263,8 +265,8 @@ extern "C" int seb_se2_lookup_vjp(const seb_grid* g, const float* poses, int64_t
     return SEB_ERR_INVALID_ARG;
   }
   if (n == 0) return SEB_OK;
-  lookup_vjp_kernel<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(args_of(g, 0.f), poses, n, gval, gpose);
-  const cudaError_t e = cudaGetLastError();
+  const cudaError_t e = seb::launch_pdl(lookup_vjp_kernel, dim3(blocks_for(n)), dim3(256), 0, (cudaStream_t)stream,
+                                        args_of(g, 0.f), poses, n, gval, gpose);
   if (e != cudaSuccess) {
     seb::set_error("seb_se2_lookup_vjp launch: %s", cudaGetErrorString(e));
     return SEB_ERR_CUDA;

@@ -56,6 +56,7 @@ __device__ __forceinline__ int64_t phys(const SdfArgs& A, int k, int i, int j) {
 }
 
 __global__ void __launch_bounds__(kColThreads) cols_kernel(const SdfArgs A) {
+  seb::pdl_entry();
   // a block per (bin, 32-column stripe): lane = column, warp = one of kSegs row segments.  Each
   // warp sweeps its segment down (distances to the nearest obstacle / free cell at or above,
   // within the segment) and records the segment's first and last obstacle / free rows; after a
@@ -130,6 +131,7 @@ __global__ void __launch_bounds__(kColThreads) cols_kernel(const SdfArgs A) {
 
 template <bool PAD>
 __global__ void __launch_bounds__(kRowThreads) rows_kernel(const SdfArgs A, int P) {
+  seb::pdl_entry();
   // squared column distances to obstacles and to free cells, [2][nx]; with PAD each row carries
   // P "no feature" sentinels on both sides ([2][P + nx + P]), so that the search reads no index
   // out of range without clamping it
@@ -242,20 +244,20 @@ extern "C" int seb_risk_sdf(const seb_grid* g, float risk_obstacle, float clamp,
   if (!(w < side)) w = side;
   A.W = (int)w;
   const cudaStream_t st = (cudaStream_t)stream;
-  cols_kernel<<<dim3((unsigned)((A.nx + 31) / 32), (unsigned)A.K), kColThreads, 0, st>>>(A);
+  cudaError_t e = seb::launch_pdl(cols_kernel, dim3((unsigned)((A.nx + 31) / 32), (unsigned)A.K), dim3(kColThreads), 0,
+                                  st, A);
   // padding of the row pass: the search reaches offset min(W, nx - 1) + 3
   const int P = min(A.W, A.nx - 1) + 4;
   const size_t psmem = (size_t)2 * (A.nx + 2 * (size_t)P) * sizeof(int32_t);
   const bool pad = psmem <= kPadSmemMax;
   const size_t rsmem = pad ? psmem : (size_t)2 * A.nx * sizeof(int32_t);
   auto rk = pad ? rows_kernel<true> : rows_kernel<false>;
-  cudaError_t e = cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
   if (e == cudaSuccess) {
     // as few passes over the row as kRowThreads allows, split evenly between the passes
     const int passes = (A.nx + kRowThreads - 1) / kRowThreads;
     const int rthreads = ((A.nx + passes - 1) / passes + 31) / 32 * 32;
-    rk<<<(unsigned)((int64_t)A.K * A.ny), rthreads, rsmem, st>>>(A, P);
-    e = cudaGetLastError();
+    e = seb::launch_pdl(rk, dim3((unsigned)((int64_t)A.K * A.ny)), dim3(rthreads), rsmem, st, A, P);
   }
   if (e != cudaSuccess) {
     seb::set_error("seb_risk_sdf launch: %s", cudaGetErrorString(e));
