@@ -392,6 +392,7 @@ __device__ __forceinline__ void stream_moments(const QTab& Q, const QLaunch& L, 
 template <typename E>
 __global__ void __launch_bounds__(256) query_fwd1_kernel(const __grid_constant__ QTab Q,
                                                          const __grid_constant__ QLaunch L) {
+  seb::pdl_entry();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L.n) return;
   float xl, yl, c, s;
@@ -406,6 +407,7 @@ __global__ void __launch_bounds__(256) query_fwd1_kernel(const __grid_constant__
 template <typename E>
 __global__ void __launch_bounds__(256) query_bwd1_kernel(const __grid_constant__ QTab Q,
                                                          const __grid_constant__ QLaunch L) {
+  seb::pdl_entry();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L.n) return;
   float xl, yl, c, s;
@@ -444,6 +446,7 @@ __global__ void __launch_bounds__(256) query_bwd1_kernel(const __grid_constant__
 template <typename E, int GL>
 __global__ void __launch_bounds__(256) query_fwd_kernel(const __grid_constant__ QTab Q,
                                                         const __grid_constant__ QLaunch L) {
+  seb::pdl_entry();
   const int gpb = 256 / GL;
   const int64_t i = (int64_t)blockIdx.x * gpb + threadIdx.x / GL;
   const int lane = threadIdx.x & (GL - 1);
@@ -462,6 +465,7 @@ __global__ void __launch_bounds__(256) query_fwd_kernel(const __grid_constant__ 
 template <typename E, int GL>
 __global__ void __launch_bounds__(256) query_bwd_kernel(const __grid_constant__ QTab Q,
                                                         const __grid_constant__ QLaunch L) {
+  seb::pdl_entry();
   const int gpb = 256 / GL;
   const int64_t i = (int64_t)blockIdx.x * gpb + threadIdx.x / GL;
   const int lane = threadIdx.x & (GL - 1);
@@ -511,9 +515,9 @@ cudaError_t launch_q(const QTab& Q, const QLaunch& L, bool backward, cudaStream_
     const int64_t blocks = (L.n + 255) / 256;
     if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
     if (backward)
-      query_bwd1_kernel<E><<<(unsigned)blocks, 256, 0, st>>>(Q, L);
+      seb::launch_pdl(query_bwd1_kernel<E>, dim3((unsigned)blocks), dim3(256), 0, st, Q, L);
     else
-      query_fwd1_kernel<E><<<(unsigned)blocks, 256, 0, st>>>(Q, L);
+      seb::launch_pdl(query_fwd1_kernel<E>, dim3((unsigned)blocks), dim3(256), 0, st, Q, L);
     return cudaGetLastError();
   }
   const int GL = Q.n <= 8 * kPPL ? 8 : 32;
@@ -522,14 +526,14 @@ cudaError_t launch_q(const QTab& Q, const QLaunch& L, bool backward, cudaStream_
   if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
   if (GL == 8) {
     if (backward)
-      query_bwd_kernel<E, 8><<<(unsigned)blocks, 256, 0, st>>>(Q, L);
+      seb::launch_pdl(query_bwd_kernel<E, 8>, dim3((unsigned)blocks), dim3(256), 0, st, Q, L);
     else
-      query_fwd_kernel<E, 8><<<(unsigned)blocks, 256, 0, st>>>(Q, L);
+      seb::launch_pdl(query_fwd_kernel<E, 8>, dim3((unsigned)blocks), dim3(256), 0, st, Q, L);
   } else {
     if (backward)
-      query_bwd_kernel<E, 32><<<(unsigned)blocks, 256, 0, st>>>(Q, L);
+      seb::launch_pdl(query_bwd_kernel<E, 32>, dim3((unsigned)blocks), dim3(256), 0, st, Q, L);
     else
-      query_fwd_kernel<E, 32><<<(unsigned)blocks, 256, 0, st>>>(Q, L);
+      seb::launch_pdl(query_fwd_kernel<E, 32>, dim3((unsigned)blocks), dim3(256), 0, st, Q, L);
   }
   return cudaGetLastError();
 }
