@@ -89,6 +89,8 @@ def parse():
     ap.add_argument("--sur-patches", type=int, default=200_000, help="surrogate training patches")
     ap.add_argument("--profile-cycle", action="store_true",
                     help="run only the local-mapping cycle row (the program profiled for its launch list)")
+    ap.add_argument("--profile-query", action="store_true",
+                    help="run three forward and three backward pose queries of 1,048,576 poses only")
     ap.add_argument("--profile-surrogate", action="store_true",
                     help="run five surrogate inferences (with the exact fallback) of the 400x400x72 map only")
     ap.add_argument("--profile-rebuild", action="store_true",
@@ -240,6 +242,35 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def profile_query():
+    """Three forward and three backward continuous-pose queries of 1,048,576 poses on the
+    100x100 map at 0.1 m (0.6x0.4 m footprint, 36 yaw bins)."""
+    import torch
+
+    import paper_2503_02412_gb300 as seb
+    from paper_2503_02412_gb300 import abi
+    from synthetic import bumpy_plane, random_poses
+
+    dev = torch.device("cuda")
+    st = torch.cuda.current_stream(dev)
+    c = seb.SebParams(nx=100, ny=100, n_yaw=36, res=0.1, length=0.6, width=0.4).c()
+    e = torch.from_numpy(bumpy_plane(0)).to(dev)
+    n = 1 << 20
+    poses = torch.from_numpy(random_poses(4, n, 100, 100, 0.1, 5)).to(dev)
+    out = torch.empty(n, 5, device=dev)
+    fl = torch.empty(n, dtype=torch.uint8, device=dev)
+    sv = torch.empty(n, abi.SEB_QUERY_SAVED, device=dev)
+    g = torch.randn(n, 5, device=dev)
+    gp = torch.empty(n, 3, device=dev)
+    for _ in range(3):
+        abi.seb_query_poses(c, e.data_ptr(), 0, 0, poses.data_ptr(), n, out.data_ptr(), fl.data_ptr(), sv.data_ptr(),
+                            st.cuda_stream)
+    for _ in range(3):
+        abi.seb_query_poses_backward(c, e.data_ptr(), 0, 0, poses.data_ptr(), sv.data_ptr(), g.data_ptr(), gp.data_ptr(),
+                                     n, st.cuda_stream)
+    torch.cuda.synchronize()
+
+
 def profile_surrogate():
     """Five surrogate inferences of the 400x400x72 fractal map with the exact fallback (weights
     from the seeded initialisation: the timing does not depend on them)."""
@@ -279,6 +310,8 @@ def main():
         return profile_rebuild()
     if args.profile_surrogate:
         return profile_surrogate()
+    if args.profile_query:
+        return profile_query()
     if args.profile_cycle:
         import torch
 
