@@ -393,21 +393,21 @@ constexpr int kQB = 4, kQBB = 2;
 
 // Moments of one pose by one thread, streaming its lattice in order (sums centred on the first
 // known point, as the grouped kernels do, but added in lattice order).
-template <typename E>
+template <typename E, int QB>
 __device__ __forceinline__ void stream_moments(const QTab& Q, const QLaunch& L, float xl, float yl, float c, float s,
                                                float m[10], float& zref) {
   for (int t = 0; t < 10; ++t) m[t] = 0.f;
   zref = 0.f;
   bool have = false;
-  for (int q0 = 0; q0 < Q.n; q0 += kQB) {
-    LatTap t[kQB];
+  for (int q0 = 0; q0 < Q.n; q0 += QB) {
+    LatTap t[QB];
 #pragma unroll
-    for (int u = 0; u < kQB; ++u) {
+    for (int u = 0; u < QB; ++u) {
       t[u].in = false;
       if (q0 + u < Q.n) lattice_fetch<E>(Q, L, q0 + u, xl, yl, c, s, t[u]);
     }
 #pragma unroll
-    for (int u = 0; u < kQB; ++u) {
+    for (int u = 0; u < QB; ++u) {
       float z, gx, gy;
       if (!lattice_eval(t[u], L, z, gx, gy)) continue;
       const float x = t[u].px, y = t[u].py;
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(256) query_fwd1_kernel(const __grid_constant__
   float xl, yl, c, s;
   pose_local(L, L.poses + 3 * i, xl, yl, c, s);
   float m[10], zref;
-  stream_moments<E>(Q, L, xl, yl, c, s, m, zref);
+  stream_moments<E, kQB>(Q, L, xl, yl, c, s, m, zref);
   QState S;
   finish_pose(Q, L, m, zref, c, s, S);
   store_pose(L, i, S);
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(256) query_bwd1_kernel(const __grid_constant__
     load_pose(L, i, c, s, S);
   } else {
     float m[10], zref;
-    stream_moments<E>(Q, L, xl, yl, c, s, m, zref);
+    stream_moments<E, kQBB>(Q, L, xl, yl, c, s, m, zref);
     finish_pose(Q, L, m, zref, c, s, S);
   }
   float gpx = 0.f, gpy = 0.f, gth = 0.f;
