@@ -6,9 +6,9 @@
 //
 // Exact and separable, in integers: the nearest known cell of (i, j) minimises
 // (i - r(j'))^2 + (j - j')^2 over the columns j', with r(j') the nearest known row of column j'.
-//   1. cols_kernel: segmented down / up sweeps per column (8 row segments per 32-column stripe,
-//      joined through their first and last known rows) store r(i, j), the nearest known row of
-//      column j to row i (the upper one on a tie), or -1.
+//   1. cols_kernel: segmented down / up sweeps per column (8, 16 or 32 row segments per 32-column
+//      stripe, by map height, joined through their first and last known rows) store r(i, j),
+//      the nearest known row of column j to row i (the upper one on a tie), or -1.
 //   2. rows_kernel: a block per row stages (i - r(j'))^2 in shared memory; each unknown cell
 //      searches outwards, s = 1, 2, ..., while s^2 does not exceed its best value.  A candidate
 //      on the left wins ties (it has the smaller column), one on the right only strict
@@ -23,19 +23,19 @@
 
 namespace {
 
-constexpr int kSegs = 8;
-constexpr int kColThreads = 32 * kSegs;
 constexpr int kRowThreads = 256;
 constexpr int kMaxSide = 16384;
 constexpr int32_t kFar = 1 << 30;  // no known cell: above any squared distance (< 2^29)
 
-__global__ void __launch_bounds__(kColThreads) nn_cols_kernel(const float* __restrict__ elev, int nx, int ny,
+// SEGS row segments (warps) per 32-column stripe: a map has few stripes, so tall maps take more.
+template <int SEGS>
+__global__ void __launch_bounds__(32 * SEGS) nn_cols_kernel(const float* __restrict__ elev, int nx, int ny,
                                                               int32_t* __restrict__ near_row) {
   seb::pdl_entry();
-  __shared__ int seg_rows[kSegs][2][32];  // last known row, first known row of each segment
+  __shared__ int seg_rows[SEGS][2][32];  // last known row, first known row of each segment
   const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
   const int j = blockIdx.x * 32 + lane;
-  const int L = (ny + kSegs - 1) / kSegs, i0 = min(ny, seg * L), i1 = min(ny, i0 + L);
+  const int L = (ny + SEGS - 1) / SEGS, i0 = min(ny, seg * L), i1 = min(ny, i0 + L);
   const bool col = j < nx;
   int last = -1, first = -1;
   if (col) {
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kColThreads) nn_cols_kernel(const float* __res
   if (!col) return;
   int above = -1, next = INT_MAX;
   for (int s = seg - 1; s >= 0 && above < 0; --s) above = seg_rows[s][0][lane];
-  for (int s = seg + 1; s < kSegs && next == INT_MAX; ++s)
+  for (int s = seg + 1; s < SEGS && next == INT_MAX; ++s)
     if (seg_rows[s][1][lane] >= 0) next = seg_rows[s][1][lane];
 #pragma unroll 4
   for (int i = i1 - 1; i >= i0; --i) {
@@ -155,8 +155,11 @@ extern "C" int seb_inpaint_nearest(const float* elev, int32_t nx, int32_t ny, in
   const int W = max_cells > 0 && max_cells < kMaxSide ? max_cells : 0;  // 0: unbounded
   int32_t* near_row = static_cast<int32_t*>(work);
   const cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e =
-      seb::launch_pdl(nn_cols_kernel, dim3((unsigned)((nx + 31) / 32)), dim3(kColThreads), 0, st, elev, nx, ny, near_row);
+  // segments of at least 8 rows, up to 32 per stripe
+  const dim3 cgrid((unsigned)((nx + 31) / 32));
+  cudaError_t e = ny >= 256  ? seb::launch_pdl(nn_cols_kernel<32>, cgrid, dim3(32 * 32), 0, st, elev, nx, ny, near_row)
+                  : ny >= 128 ? seb::launch_pdl(nn_cols_kernel<16>, cgrid, dim3(32 * 16), 0, st, elev, nx, ny, near_row)
+                              : seb::launch_pdl(nn_cols_kernel<8>, cgrid, dim3(32 * 8), 0, st, elev, nx, ny, near_row);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(nn_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(nx * sizeof(int32_t)));
   if (e == cudaSuccess)

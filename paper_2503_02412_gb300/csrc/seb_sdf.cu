@@ -12,9 +12,9 @@
 // Exact Euclidean distances, separable: d^2(i, j) = min_j' g(i, j')^2 + (j - j')^2, with
 // g(i, j') the distance in rows to the nearest feature of column j'.  Nothing farther than
 // W = ceil(clamp / res) + 1 cells can fall under the clamp, so W bounds both passes.
-//   1. cols_kernel: sweeps every column down and up (linear time), split in 8 row segments swept
-//      by separate warps and joined through their first / last obstacle and free rows, and
-//      stores per cell the distance in rows to the nearest obstacle and to the nearest free cell
+//   1. cols_kernel: sweeps every column down and up (linear time), split in 8 row segments (16 on
+//      small grids) swept by separate warps and joined through their first / last obstacle and
+//      free rows, and stores per cell the distance in rows to the nearest obstacle and to the nearest free cell
 //      of its column (uint16 each, 0xFFFF = none within W).  Loads are issued 8 rows at a time.
 //   2. rows_kernel: a block per (bin, row) stages that row's squared column distances in shared
 //      memory, padded with "no feature" sentinels; every cell takes the minimum of
@@ -32,8 +32,6 @@ namespace {
 
 constexpr uint32_t kNone = 0xFFFFu;
 constexpr int kMaxSide = 16384;
-constexpr int kSegs = 8;
-constexpr int kColThreads = 32 * kSegs;
 constexpr int kBatch = 8;      // column-pass loads in flight per thread
 constexpr int kRowThreads = 256;
 constexpr size_t kPadSmemMax = 96 * 1024;  // padded row pass up to this much shared memory
@@ -55,16 +53,18 @@ __device__ __forceinline__ int64_t phys(const SdfArgs& A, int k, int i, int j) {
   return ((int64_t)k * A.ny + r) * A.nx + c;
 }
 
-__global__ void __launch_bounds__(kColThreads) cols_kernel(const SdfArgs A) {
+// SEGS row segments (warps) per column stripe: more of them when the grid has few stripes.
+template <int SEGS>
+__global__ void __launch_bounds__(32 * SEGS) cols_kernel(const SdfArgs A) {
   seb::pdl_entry();
-  // a block per (bin, 32-column stripe): lane = column, warp = one of kSegs row segments.  Each
+  // a block per (bin, 32-column stripe): lane = column, warp = one of SEGS row segments.  Each
   // warp sweeps its segment down (distances to the nearest obstacle / free cell at or above,
   // within the segment) and records the segment's first and last obstacle / free rows; after a
   // barrier it sweeps up, completing each distance with the nearest rows of the other segments.
-  __shared__ int seg_rows[kSegs][4][32];  // last obstacle, first obstacle, last free, first free
+  __shared__ int seg_rows[SEGS][4][32];  // last obstacle, first obstacle, last free, first free
   const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
   const int j = blockIdx.x * 32 + lane, k = blockIdx.y;
-  const int L = (A.ny + kSegs - 1) / kSegs, i0 = min(A.ny, seg * L), i1 = min(A.ny, i0 + L);
+  const int L = (A.ny + SEGS - 1) / SEGS, i0 = min(A.ny, seg * L), i1 = min(A.ny, i0 + L);
   const bool col = j < A.nx;
   uint32_t* out = A.work + (int64_t)k * A.ny * A.nx + j;
   int last_o = -1, first_o = -1, last_f = -1, first_f = -1;
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kColThreads) cols_kernel(const SdfArgs A) {
     if (above_o < 0) above_o = seg_rows[s2][0][lane];
     if (above_f < 0) above_f = seg_rows[s2][2][lane];
   }
-  for (int s2 = seg + 1; s2 < kSegs; ++s2) {
+  for (int s2 = seg + 1; s2 < SEGS; ++s2) {
     if (next_o == INT_MAX && seg_rows[s2][1][lane] >= 0) next_o = seg_rows[s2][1][lane];
     if (next_f == INT_MAX && seg_rows[s2][3][lane] >= 0) next_f = seg_rows[s2][3][lane];
   }
@@ -244,8 +244,10 @@ extern "C" int seb_risk_sdf(const seb_grid* g, float risk_obstacle, float clamp,
   if (!(w < side)) w = side;
   A.W = (int)w;
   const cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = seb::launch_pdl(cols_kernel, dim3((unsigned)((A.nx + 31) / 32), (unsigned)A.K), dim3(kColThreads), 0,
-                                  st, A);
+  // 16 row segments per stripe when the grid has few stripes (a small map), else 8
+  const dim3 cgrid((unsigned)((A.nx + 31) / 32), (unsigned)A.K);
+  cudaError_t e = (int64_t)cgrid.x * cgrid.y < 600 ? seb::launch_pdl(cols_kernel<16>, cgrid, dim3(32 * 16), 0, st, A)
+                                                  : seb::launch_pdl(cols_kernel<8>, cgrid, dim3(32 * 8), 0, st, A);
   // padding of the row pass: the search reaches offset min(W, nx - 1) + 3
   const int P = min(A.W, A.nx - 1) + 4;
   const size_t psmem = (size_t)2 * (A.nx + 2 * (size_t)P) * sizeof(int32_t);
