@@ -163,6 +163,7 @@ __global__ void raycast_kernel(ElevArgs A, const double* __restrict__ pw, const 
     const int stx = dx > 0 ? 1 : (dx < 0 ? -1 : 0), sty = dy > 0 ? 1 : (dy < 0 ? -1 : 0);
     const int64_t ei = (int64_t)floor(ex), ej = (int64_t)floor(ey);
     const double ts = (double)seg / kRaySegs, te = (double)(seg + 1) / kRaySegs;
+    const bool up = dz > 0.0;
     int64_t ci = (int64_t)floor(seg == 0 ? sx : sx + dx * ts), cj = (int64_t)floor(seg == 0 ? sy : sy + dy * ts);
     // next boundary crossings and the entry time of the start cell
     double tmx = stx > 0 ? ((double)(ci + 1) - sx) * ix : (stx < 0 ? ((double)ci - sx) * ix : INFINITY);
@@ -188,9 +189,11 @@ __global__ void raycast_kernel(ElevArgs A, const double* __restrict__ pw, const 
         if (t1 > t0 && ci >= A.oi && ci < A.oi + A.nx && cj >= A.oj && cj < A.oj + A.ny) {
           act[u] = true;
           kc[u] = store_idx(A, ci, cj);
-          top[u] = fmax(sz + dz * t0, sz + dz * t1);
+          // the ray's highest height over the cell: at its exit if it climbs, else at its entry
+          // (the same double as the larger of the two, since the rounding of sz + dz t is monotone)
+          top[u] = sz + dz * (up ? t1 : t0);
         }
-        if (t1 >= 1.0 || t1 >= te) {  // the next cell is entered at or after this segment's end
+        if (t1 >= te) {  // the next cell is entered at or after this segment's end (te <= 1)
           done = true;
           continue;
         }
@@ -314,6 +317,14 @@ bool params_ok(const seb_elev_params* p) {
 int blocks_for(int64_t n) {
   const int64_t b = (n + 255) / 256;
   return (int)(b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8);
+}
+
+// The ray walks are few (~1e5 segments) and uneven in length: small blocks spread them over the
+// SMs more evenly.
+constexpr int kRayThreads = 64;
+int ray_blocks(int64_t n) {
+  const int64_t b = (n + kRayThreads - 1) / kRayThreads;
+  return (int)(b < 152 * 32 ? (b > 0 ? b : 1) : 152 * 32);
 }
 
 int fail(int code, const char* msg) {
@@ -452,7 +463,7 @@ int seb_elev_integrate(seb_elev* e, const seb_scan_pose* pose, const float* pts,
     err = seb::launch_pdl(points_kernel, dim3(blocks_for(n)), dim3(256), 0, st, A, pts, n, e->cell, e->pz, e->inside,
                           e->pw, e->rinv);
   if (n > 0 && err == cudaSuccess)
-    err = seb::launch_pdl(raycast_kernel, dim3(blocks_for(n * kRaySegs)), dim3(256), 0, st, A, e->pw, e->rinv,
+    err = seb::launch_pdl(raycast_kernel, dim3(ray_blocks(n * kRaySegs)), dim3(kRayThreads), 0, st, A, e->pw, e->rinv,
                           e->inside, n, e->h, e->s2);
   if (n > 0 && err == cudaSuccess)
     err = seb::launch_pdl(accumulate_kernel, dim3(blocks_for(n)), dim3(256), 0, st, A, e->cell, e->pz, n, e->h, e->s2,
