@@ -2,7 +2,9 @@
 """Benchmark of the SE(2)-grid traversability hot path on the full local map:
 400 x 400 cells at 0.05 m, 72 yaw bins, 0.9 x 0.6 m footprint, fractal terrain with steps and
 5 % unknown cells.  One step = a full rebuild of the map (11.52 M SE(2) cells) followed by 50
-rolling shifts of 10 cells in random directions, each recomputing only the affected bands.
+rolling shifts of 10 cells in random directions, each recomputing only the affected bands (the
+50 moves go through one seb_map_shift_batch call; their time as 50 separate seb_map_shift calls
+is reported beside it).
 
 Prints one JSON line.  value = SE(2) cells assessed per second over the timed steps (cells
 actually recomputed: the rebuild plus every shift band), whole job over all ranks.
@@ -351,9 +353,8 @@ def main():
         if ev_rebuild is not None:
             ev_rebuild[1].record(stream)
         cells = m.view().last_cells
-        for w, o in zip(wins[1:], origins[1:]):
-            m.shift(w, o)
-            cells += m.view().last_cells
+        m.shift_batch(wins[1:], origins[1:])
+        cells += m.view().last_cells
         return cells
 
     for _ in range(args.warmup):
@@ -385,6 +386,15 @@ def main():
         torch.distributed.barrier()
     ms_per_step = total_ms / args.steps
     value = job_value(cells_total, world_size, total_ms)
+    # the same 50 moves as separate seb_map_shift calls (each waits for the previous kernel)
+    m.update(wins[0], origins[0])
+    es = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    es[0].record(stream)
+    for w, o in zip(wins[1:], origins[1:]):
+        m.shift(w, o)
+    es[1].record(stream)
+    es[1].synchronize()
+    shift_single_us = es[0].elapsed_time(es[1]) / N_SHIFTS * 1e3
 
     # roofline of the dominant kernel (the full-map rebuild launch)
     props = torch.cuda.get_device_properties(dev)
@@ -413,6 +423,7 @@ def main():
                    "l2": "flushed before every timed step (256 MB write)"},
         "rebuild_ms": rb, "rebuild_cells_per_s": NX * NY * K / (rb * 1e-3),
         "shift_us_mean": (ms_per_step - rb) / N_SHIFTS * 1e3,
+        "shift_us_mean_single_calls": shift_single_us,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "assess_kernel_sl<float> (rebuild)",
                      "flop_per_launch": flop, "flop_basis": "algorithmic: 9 N + 200 per cell and yaw pair (N footprint points)",
@@ -647,44 +658,44 @@ def abi_inpaint_bytes(seb, n):
 
 def run_e2e(seb, m, world_np, origins, args, dev):
     """Same step through the public API with host buffers, pipelined as an application would run
-    it: every window is copied host -> device from pinned memory on an upload stream (a ring of 3
-    device buffers, ordered by events) ahead of its update/shift; at the end of the step the
+    it: the step's windows (one pinned host array) are copied host -> device on an upload stream
+    into one of two device window sets while the previous step computes; the compute stream
+    waits for its set, then runs the rebuild and the shift batch; at the end of the step the
     outputs (5 channels + flags, in window order) are snapshotted with copy_out and read back to
     pinned host memory on a download stream while the next step computes.  The timed region
     covers all steps and ends when the last read-back has landed in host memory."""
     import torch
 
-    host_wins = [torch.from_numpy(np.ascontiguousarray(world_np[o[1]:o[1] + NY, o[0]:o[0] + NX])).pin_memory()
-                 for o in origins]
-    nb = 3
-    dwins = [torch.empty((NY, NX), dtype=torch.float32, device=dev) for _ in range(nb)]
+    n = len(origins)
+    host_set = torch.from_numpy(np.stack([world_np[o[1]:o[1] + NY, o[0]:o[0] + NX] for o in origins])).pin_memory()
+    dsets = [torch.empty((n, NY, NX), dtype=torch.float32, device=dev) for _ in range(2)]
     stage = torch.empty((5, K, NY, NX), dtype=torch.float32, device=dev)
     stage_fl = torch.empty((K, NY, NX), dtype=torch.uint8, device=dev)
     hout = torch.empty(stage.numel(), dtype=torch.float32).pin_memory()
     hfl = torch.empty(stage_fl.numel(), dtype=torch.uint8).pin_memory()
     comp = torch.cuda.current_stream(dev)
     up, down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-    win_ready = [torch.cuda.Event() for _ in range(nb)]
-    win_free = [torch.cuda.Event() for _ in range(nb)]
+    set_ready = [torch.cuda.Event() for _ in range(2)]
+    set_free = [torch.cuda.Event() for _ in range(2)]
     stage_ready, stage_free = torch.cuda.Event(), torch.cuda.Event()
-    h2d = sum(w.numel() * 4 for w in host_wins)
+    h2d = host_set.numel() * 4
     d2h = hout.numel() * 4 + hfl.numel()
+    state = {"k": 0}
 
     def step():
-        cells = 0
-        for i, (hw, o) in enumerate(zip(host_wins, origins)):
-            k = i % nb
-            with torch.cuda.stream(up):
-                up.wait_event(win_free[k])  # the shift that last read this buffer is done
-                dwins[k].copy_(hw, non_blocking=True)
-                win_ready[k].record(up)
-            comp.wait_event(win_ready[k])
-            if i == 0:
-                m.update(dwins[k], o)
-            else:
-                m.shift(dwins[k], o)
-            win_free[k].record(comp)
-            cells += m.view().last_cells
+        k = state["k"]
+        state["k"] ^= 1
+        ws = dsets[k]
+        with torch.cuda.stream(up):
+            up.wait_event(set_free[k])  # the batch that last read this set is done
+            ws.copy_(host_set, non_blocking=True)
+            set_ready[k].record(up)
+        comp.wait_event(set_ready[k])
+        m.update(ws[0], origins[0])
+        cells = m.view().last_cells
+        m.shift_batch([ws[i] for i in range(1, n)], origins[1:])
+        cells += m.view().last_cells
+        set_free[k].record(comp)
         comp.wait_event(stage_free)  # the previous read-back has left the staging buffers
         m.outputs(stage, stage_fl)
         stage_ready.record(comp)
@@ -707,10 +718,10 @@ def run_e2e(seb, m, world_np, origins, args, dev):
     e1.record(comp)
     e1.synchronize()
     total = e0.elapsed_time(e1)
-    ws = int(os.environ.get("WORLD_SIZE", 1))
-    return {"value": cells * ws / (total / 1e3), "unit": "SE(2) cells/s", "h2d_bytes_per_step": h2d,
+    ws_n = int(os.environ.get("WORLD_SIZE", 1))
+    return {"value": cells * ws_n / (total / 1e3), "unit": "SE(2) cells/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": total / args.steps,
-            "pipeline": "uploads and read-backs on their own streams, overlapped with the updates"}
+            "pipeline": "window uploads and output read-backs on their own streams, overlapped with the updates"}
 
 
 if __name__ == "__main__":

@@ -158,12 +158,24 @@ int seb_map_update(seb_map* m, const void* elev_dev, int64_t origin_i, int64_t o
  * whole new window in logical order.  The ring offsets advance by the move, and only the
  * cells whose footprint can see a cell that entered or left the window are recomputed:
  * a band of |move| + reach cells on the entering side and of reach cells on the leaving
- * side, per axis (reach = largest |offset| of any footprint along that axis, plus 3 columns
- * / 1 row: cells are computed in 4 x 2 blocks that share a reference height).  Every other
- * cell keeps its stored value, which is bit-identical to a full rebuild.  A move of at
- * least the window size in either axis falls back to a full rebuild.
+ * side, per axis (reach = largest |offset| of any footprint along that axis), each widened to
+ * whole 4 x 2 cell blocks in world alignment (the cells of a block share a reference height).
+ * Every other cell keeps its stored value, which is bit-identical to a full rebuild.  A move of
+ * at least the window size in either axis falls back to a full rebuild.
  */
 int seb_map_shift(seb_map* m, const void* elev_dev, int64_t origin_i, int64_t origin_j);
+
+/*
+ * n rolling updates in order (Sec. V-A), with results bit-identical to n seb_map_shift calls:
+ * elev_dev[i] (a host array of n device pointers) is the whole window of the i-th move, and
+ * origins[2 i], origins[2 i + 1] (a host array) its origin.  All n windows must be written, in
+ * the map's stream order, before this call; none may be overwritten until the call's work has
+ * completed.  Each launch after the first may then stage and compute while the previous one is
+ * still finishing, and it stores only after that one completes, which fills the GPU across the
+ * moves.  view.last_cells afterwards counts the cells recomputed by the whole batch.  On an
+ * error the moves before the failing one have been applied.
+ */
+int seb_map_shift_batch(seb_map* m, const void* const* elev_dev, const int64_t* origins, int32_t n);
 
 /* Pointers and ring offsets of the current outputs. */
 int seb_map_view(const seb_map* m, seb_view* v);

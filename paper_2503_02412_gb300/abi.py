@@ -42,6 +42,7 @@ EXPORTS = (
     "seb_map_set_stream",
     "seb_map_update",
     "seb_map_shift",
+    "seb_map_shift_batch",
     "seb_map_view",
     "seb_map_copy_out",
     "seb_map_check",
@@ -211,6 +212,7 @@ def load():
             "seb_map_set_stream": (ctypes.c_int, [vp, vp]),
             "seb_map_update": (ctypes.c_int, [vp, vp, i64, i64]),
             "seb_map_shift": (ctypes.c_int, [vp, vp, i64, i64]),
+            "seb_map_shift_batch": (ctypes.c_int, [vp, ctypes.POINTER(vp), i64p, i32]),
             "seb_map_view": (ctypes.c_int, [vp, ctypes.POINTER(seb_view)]),
             "seb_map_copy_out": (ctypes.c_int, [vp, vp, vp]),
             "seb_map_check": (ctypes.c_int, [vp, i32, i64p, i64p]),
@@ -313,6 +315,14 @@ def seb_map_update(handle: int, elev_ptr: int, origin_i: int, origin_j: int) -> 
 
 def seb_map_shift(handle: int, elev_ptr: int, origin_i: int, origin_j: int) -> None:
     _check(load().seb_map_shift(handle, elev_ptr, origin_i, origin_j), handle)
+
+
+def seb_map_shift_batch(handle: int, elev_ptrs, origins) -> None:
+    """elev_ptrs: n device pointers (ints); origins: n (origin_i, origin_j) pairs."""
+    n = len(elev_ptrs)
+    ptrs = (ctypes.c_void_p * max(n, 1))(*[ctypes.c_void_p(int(x)) for x in elev_ptrs])
+    org = (ctypes.c_int64 * max(2 * n, 1))(*[int(v) for o in origins for v in (o[0], o[1])])
+    _check(load().seb_map_shift_batch(handle, ptrs, org, n), handle)
 
 
 def seb_map_view(handle: int) -> seb_view:

@@ -206,7 +206,7 @@ int seb_map_set_stream(seb_map* m, seb_stream_t s) {
   return SEB_OK;
 }
 
-int seb_map_update(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
+static int update_impl(seb_map* m, const void* elev, int64_t oi, int64_t oj, int early) {
   if (!m) return fail(nullptr, SEB_ERR_INVALID_ARG, "map is NULL");
   int rc = check_elev(m, elev);
   if (rc) return rc;
@@ -215,6 +215,7 @@ int seb_map_update(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
   m->ring_x = (int32_t)(((oi % m->p.nx) + m->p.nx) % m->p.nx);
   m->ring_y = (int32_t)(((oj % m->p.ny) + m->p.ny) % m->p.ny);
   Launch L = base_launch(m, elev);
+  L.early = early;
   launch_set_origin(L, oi, oj);
   launch_request(L, 0, 0, m->p.nx, m->p.ny);
   cudaError_t e = launch_assess(m->T, L, m->p.elev_dtype, m->p.precision, m->stream);
@@ -226,14 +227,16 @@ int seb_map_update(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
   return SEB_OK;
 }
 
-int seb_map_shift(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
+int seb_map_update(seb_map* m, const void* elev, int64_t oi, int64_t oj) { return update_impl(m, elev, oi, oj, 0); }
+
+static int shift_impl(seb_map* m, const void* elev, int64_t oi, int64_t oj, int early) {
   if (!m) return fail(nullptr, SEB_ERR_INVALID_ARG, "map is NULL");
-  if (!m->valid) return seb_map_update(m, elev, oi, oj);
+  if (!m->valid) return update_impl(m, elev, oi, oj, early);
   int rc = check_elev(m, elev);
   if (rc) return rc;
   const int64_t dx = oi - m->oi, dy = oj - m->oj;
   const int nx = m->p.nx, ny = m->p.ny;
-  if (dx >= nx || -dx >= nx || dy >= ny || -dy >= ny) return seb_map_update(m, elev, oi, oj);
+  if (dx >= nx || -dx >= nx || dy >= ny || -dy >= ny) return update_impl(m, elev, oi, oj, early);
   if (dx == 0 && dy == 0) {
     m->last_cells = 0;
     return SEB_OK;
@@ -269,6 +272,7 @@ int seb_map_shift(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
   if (top > 0) top += (2 - (top + py) % 2) % 2;
   if (bottom > 0) bottom += (ny - bottom + py) % 2;
   Launch L = base_launch(m, elev);
+  L.early = early;
   launch_set_origin(L, oi, oj);
   if (left + right >= nx || top + bottom >= ny) {
     launch_request(L, 0, 0, nx, ny);
@@ -283,6 +287,23 @@ int seb_map_shift(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
   m->last_cells = rect_cells(L, m->p.n_yaw);
   m->oi = oi;
   m->oj = oj;
+  return SEB_OK;
+}
+
+int seb_map_shift(seb_map* m, const void* elev, int64_t oi, int64_t oj) { return shift_impl(m, elev, oi, oj, 0); }
+
+int seb_map_shift_batch(seb_map* m, const void* const* elev, const int64_t* origins, int32_t n) {
+  if (!m) return fail(nullptr, SEB_ERR_INVALID_ARG, "map is NULL");
+  if (n < 0 || (n > 0 && (!elev || !origins)))
+    return fail(m, SEB_ERR_INVALID_ARG, "shift batch: NULL window or origin array, or negative count");
+  int64_t cells = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    // the first launch waits for everything before the batch; the later ones may start early
+    const int rc = shift_impl(m, elev[i], origins[2 * i], origins[2 * i + 1], i > 0 ? 1 : 0);
+    if (rc) return rc;
+    cells += m->last_cells;
+  }
+  m->last_cells = cells;
   return SEB_OK;
 }
 

@@ -424,8 +424,16 @@ __global__ void __launch_bounds__(kThreads, 2)
   int* rowflag = reinterpret_cast<int*>(smem);
   float2* qs = reinterpret_cast<float2*>(smem + kMaxStageRows);  // [kSlQ][kThreads]
   float2* pt = qs + kSlQ * kThreads;                             // [sh - 1][sw2] vertical pairs
-  pdl_entry();  // no global memory access before the stream's previous kernel has completed
+  // No global memory access before the stream's previous kernel has completed (pdl_entry) ...
+  // except in a later launch of one shift batch: its input window was written before the batch
+  // began, and the batch's first launch waited for that before any later launch could start, so
+  // it stages and computes at once and waits for the previous launch only before its first store.
+  if (L.early)
+    asm volatile("griddepcontrol.launch_dependents;");
+  else
+    pdl_entry();
   if (blockDim.x != kThreads || blockIdx.y >= (unsigned)T.n_pairs) {
+    if (L.early) asm volatile("griddepcontrol.wait;" ::: "memory");
     if (threadIdx.x == 0) atomicOr(L.err, kErrLaunchShape);
     return;
   }
@@ -637,6 +645,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
   }
 
+  if (L.early) asm volatile("griddepcontrol.wait;" ::: "memory");  // the previous launch's stores first
   const int k0 = pair, k1 = pair + T.n_pairs;
   const float ct = T.cos_t[pair], st = T.sin_t[pair];
   const int64_t chs = (int64_t)L.n_yaw * L.plane;

@@ -61,6 +61,7 @@ struct Launch {
   Rect req[4];
   int32_t phase_x, phase_y;  // window origin mod 4 / mod 2 (global alignment of cell blocks)
   int32_t vec4;              // whole 4-cell blocks may be stored with 16-byte stores
+  int32_t early;             // a later launch of a shift batch (seb_map_shift_batch): see the kernel
   int32_t n_rects;
   Rect rects[kMaxRects];
   int32_t tile_start[kMaxRects + 1];

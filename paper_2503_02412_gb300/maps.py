@@ -104,6 +104,17 @@ class SebMap:
         abi.seb_map_set_stream(self.handle, _stream(self.device))
         abi.seb_map_shift(self.handle, elev.data_ptr(), int(origin[0]), int(origin[1]))
 
+    def shift_batch(self, elevs, origins):
+        """Rolling updates to origins[i] with windows elevs[i], in order; bit-identical to
+        calling shift for each.  The windows must all be written before the call and stay
+        untouched until its work on the stream has completed."""
+        if len(elevs) != len(origins):
+            raise ValueError("one origin per window")
+        for e in elevs:
+            self._check_elev(e)
+        abi.seb_map_set_stream(self.handle, _stream(self.device))
+        abi.seb_map_shift_batch(self.handle, [e.data_ptr() for e in elevs], [(int(o[0]), int(o[1])) for o in origins])
+
     def view(self):
         return abi.seb_map_view(self.handle)
 

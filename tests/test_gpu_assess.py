@@ -187,6 +187,48 @@ def test_rolling_window_bit_identical_to_rebuild(seb):
     compare(g, gf, ref, rfl, label="rolling sample", gap=gap)
 
 
+def test_shift_batch_equals_single_shifts(seb):
+    """seb_map_shift_batch (later launches stage and compute while the previous one finishes)
+    gives the same bits as one seb_map_shift per move: 40 random moves with a zero move, a move
+    beyond the window (a full rebuild inside the batch) and moves after it, then a second batch
+    on the same map, after which the map equals a fresh rebuild of the final window."""
+    world = fractal_world(4, 1700)
+    tw = torch.from_numpy(world).cuda()
+    p = seb.SebParams(**C2)
+    win = lambda o: tw[o[1]:o[1] + 400, o[0]:o[0] + 400].contiguous()  # noqa: E731
+    o = [650, 650]
+    origins = []
+    for k, (dx, dy) in enumerate(shift_sequence(7, 40)):
+        if k == 11:
+            dx, dy = 0, 0
+        if k == 23:
+            dx, dy = 450, -20  # beyond the window: a full rebuild
+        o = [min(max(o[0] + dx, 0), 1300), min(max(o[1] + dy, 0), 1300)]
+        origins.append(tuple(o))
+    wins = [win(q) for q in origins]
+    start = (650, 650)
+    single = seb.SebMap(p)
+    single.update(win(start), start)
+    for w, q in zip(wins, origins):
+        single.shift(w, q)
+    batch = seb.SebMap(p)
+    batch.update(win(start), start)
+    batch.shift_batch(wins[:25], origins[:25])
+    assert batch.view().last_cells > 0
+    batch.shift_batch(wins[25:], origins[25:])
+    so, sf = single.outputs()
+    bo, bf = batch.outputs()
+    assert torch.equal(so.view(torch.int32), bo.view(torch.int32)) and torch.equal(sf, bf)
+    full = seb.SebMap(p)
+    full.update(win(origins[-1]), origins[-1])
+    fo, ff = full.outputs()
+    assert torch.equal(bo.view(torch.int32), fo.view(torch.int32)) and torch.equal(bf, ff)
+    batch.check()
+    single.check()
+    with pytest.raises(ValueError):
+        batch.shift_batch(wins[:2], origins[:1])
+
+
 @pytest.mark.parametrize("move", [(0, 0), (1, 0), (0, -1), (-7, 13), (399, 0), (400, 5), (-1000, 2000)])
 def test_shift_edge_moves(seb, move):
     world = fractal_world(3, 1400)
