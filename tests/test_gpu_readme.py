@@ -26,6 +26,10 @@ def test_quick_start_usage():
     m = seb.SebMap(p)
     m.update(elev, origin=(oi, oj))
     m.shift(next_elev, origin=(oi + 10, oj - 3))
+    origins = [(oi + 10 + 2 * k, oj - 3 - k) for k in range(1, 4)]
+    windows = [world[q[1]:q[1] + n, q[0]:q[0] + n].contiguous() for q in origins]
+    m.shift_batch(windows, origins)
+    m.shift(world[oj - 3:oj - 3 + n, oi + 10:oi + 10 + n].contiguous(), origin=(oi + 10, oj - 3))
     out, flags = m.outputs()
     assert tuple(out.shape) == (5, 72, n, n) and tuple(flags.shape) == (72, n, n)
     m.check()
