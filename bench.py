@@ -426,7 +426,8 @@ def main():
         "shift_us_mean_single_calls": shift_single_us,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "assess_kernel_sl<float> (rebuild)",
-                     "flop_per_launch": flop, "flop_basis": "algorithmic: 9 N + 200 per cell and yaw pair (N footprint points)",
+                     "flop_per_launch": flop,
+                     "flop_basis": "algorithmic: 9 N + 200 per cell and yaw pair (N footprint points)",
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x 2070 MHz",
                      "executed": {"flop_per_launch": flop_exec, "achieved": achieved_exec, "frac": achieved_exec / peak,
                                   "flop_basis": "sliding row sums as run: 1.5 N + 15.5 R + 200 per cell and yaw pair"}},

@@ -163,8 +163,8 @@ extern "C" int seb_inpaint_nearest(const float* elev, int32_t nx, int32_t ny, in
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(nn_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(nx * sizeof(int32_t)));
   if (e == cudaSuccess)
-    e = seb::launch_pdl(nn_rows_kernel, dim3((unsigned)ny), dim3(kRowThreads), nx * sizeof(int32_t), st, elev, near_row, nx,
-                        ny, W, out, src);
+    e = seb::launch_pdl(nn_rows_kernel, dim3((unsigned)ny), dim3(kRowThreads), nx * sizeof(int32_t), st, elev,
+                        near_row, nx, ny, W, out, src);
   if (e != cudaSuccess) {
     seb::set_error("seb_inpaint_nearest launch: %s", cudaGetErrorString(e));
     return SEB_ERR_CUDA;

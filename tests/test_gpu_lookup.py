@@ -119,7 +119,8 @@ def test_max_yaw_bins(seb):
     grid = random_se2_grid(31, K2, ny, nx)
     rng = np.random.default_rng(32)
     n = 50_000
-    P = np.stack([(ORIGIN[0] + rng.uniform(0, nx - 1, n) + 0.5) * RES, (ORIGIN[1] + rng.uniform(0, ny - 1, n) + 0.5) * RES,
+    P = np.stack([(ORIGIN[0] + rng.uniform(0, nx - 1, n) + 0.5) * RES,
+                  (ORIGIN[1] + rng.uniform(0, ny - 1, n) + 0.5) * RES,
                   rng.uniform(-1e4, 1e4, n)], 1).astype(np.float32)
     ring = (3, 2)
     g = seb.SE2Grid.from_tensor(torch.from_numpy(grid).cuda(), RES, ORIGIN, ring)
