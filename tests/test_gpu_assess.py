@@ -229,6 +229,48 @@ def test_shift_batch_equals_single_shifts(seb):
         batch.shift_batch(wins[:2], origins[:1])
 
 
+@pytest.mark.parametrize("cfg,seed", [(dict(nx=200, ny=120, n_yaw=36, res=0.05, length=0.9, width=0.6), 11),
+                                      (dict(nx=96, ny=160, n_yaw=8, res=0.1, length=1.5, width=0.6, shape="ellipse"), 12)])
+def test_shift_batch_stress(seb, cfg, seed):
+    """Batches with runs of zero moves, moves past the window (full rebuilds inside the batch),
+    one-cell moves and a one-element batch, on a non-square map and an ellipse footprint: the
+    same bits as separate seb_map_shift calls."""
+    rng = np.random.default_rng(seed)
+    world = fractal_world(seed, 900, cfg["res"])
+    tw = torch.from_numpy(world).cuda()
+    p = seb.SebParams(**cfg)
+    nx, ny = cfg["nx"], cfg["ny"]
+    win = lambda o: tw[o[1]:o[1] + ny, o[0]:o[0] + nx].contiguous()  # noqa: E731
+    o = [300, 300]
+    origins = []
+    for k in range(60):
+        r = rng.random()
+        if r < 0.2:
+            d = (0, 0)
+        elif r < 0.3:
+            d = (int(rng.choice([-1, 1]) * nx), int(rng.integers(-3, 4)))
+        elif r < 0.5:
+            d = (int(rng.integers(-1, 2)), int(rng.integers(-1, 2)))
+        else:
+            d = (int(rng.integers(-25, 26)), int(rng.integers(-25, 26)))
+        o = [min(max(o[0] + d[0], 0), 900 - nx), min(max(o[1] + d[1], 0), 900 - ny)]
+        origins.append(tuple(o))
+    wins = [win(q) for q in origins]
+    single, batch = seb.SebMap(p), seb.SebMap(p)
+    for mm in (single, batch):
+        mm.update(win((300, 300)), (300, 300))
+    for w, q in zip(wins, origins):
+        single.shift(w, q)
+    cuts = [0, 1, 17, 18, 40, 60]
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        batch.shift_batch(wins[a:b], origins[a:b])
+    so, sf = single.outputs()
+    bo, bf = batch.outputs()
+    assert torch.equal(so.view(torch.int32), bo.view(torch.int32)) and torch.equal(sf, bf)
+    single.check()
+    batch.check()
+
+
 @pytest.mark.parametrize("move", [(0, 0), (1, 0), (0, -1), (-7, 13), (399, 0), (400, 5), (-1000, 2000)])
 def test_shift_edge_moves(seb, move):
     world = fractal_world(3, 1400)
