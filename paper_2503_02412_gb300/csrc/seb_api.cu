@@ -298,8 +298,9 @@ int seb_map_shift_batch(seb_map* m, const void* const* elev, const int64_t* orig
     return fail(m, SEB_ERR_INVALID_ARG, "shift batch: NULL window or origin array, or negative count");
   int64_t cells = 0;
   for (int32_t i = 0; i < n; ++i) {
-    // the first launch waits for everything before the batch; the later ones may start early
-    const int rc = shift_impl(m, elev[i], origins[2 * i], origins[2 * i + 1], i > 0 ? 1 : 0);
+    // The first launch of the batch waits for everything before it; the later ones may start
+    // early.  A zero move launches nothing, so "first" is counted in launches, not in moves.
+    const int rc = shift_impl(m, elev[i], origins[2 * i], origins[2 * i + 1], cells > 0 ? 1 : 0);
     if (rc) return rc;
     cells += m->last_cells;
   }
