@@ -17,6 +17,7 @@ same workload's cells per step); under torchrun only rank 0 runs it.
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import os
@@ -81,7 +82,7 @@ def kernel_sources_sha():
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
@@ -147,47 +148,74 @@ def cpu_baseline(world, origins, budget_s, rng_seed=0):
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling of the SM clock and the throttle reasons.  Sampling is live before
+    start() returns, and only the samples stamped between start() and stop() count."""
+
+    INTERVAL_MS = 50
 
     def __init__(self, index):
         d = os.environ.get("SEB_CLOCKS_DIR", tempfile.gettempdir())
         self.path = os.path.join(d, f"seb_clocks_rank{index}.csv")
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        self.t0 = self.t1 = None
         try:
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}", "--format=csv,noheader",
-                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                       "-lms", str(self.INTERVAL_MS)], stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.p = None
+            return
+        deadline = time.time() + 10.0  # the first sample: nvidia-smi has started
+        while time.time() < deadline and self.p.poll() is None and os.path.getsize(self.path) == 0:
+            time.sleep(0.02)
+
+    def start(self):
+        self.t0 = time.time()
 
     def stop(self):
+        self.t1 = time.time()
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.25)
+        time.sleep(2 * self.INTERVAL_MS / 1e3)  # the sample in flight lands
         self.p.terminate()
         self.p.wait()
         self.f.close()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1].split()[0]))
-                smax.append(float(parts[2].split()[0]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return summarise_clocks(open(self.path).read().splitlines(), self.t0, self.t1)
+
+
+def summarise_clocks(lines, t0, t1):
+    """Median SM clock, maximum clock and the throttle reasons seen in the samples stamped
+    within [t0, t1] (host epoch seconds).  A region shorter than the sampling interval holds
+    no sample; it then takes the one nearest its middle and says so."""
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    rows = []
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 10:
+            continue
+        try:
+            ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            sm, smax = float(parts[2].split()[0]), float(parts[3].split()[0])
+        except ValueError:
+            continue
+        rows.append((ts, sm, smax, [nm for nm, v in zip(names, parts[6:10]) if v.lower().startswith("active")]))
+    if not rows:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+    inside = [r for r in rows if t0 is not None and t0 <= r[0] <= t1]
+    note = None
+    if not inside:
+        mid = 0.5 * (t0 + t1) if t0 is not None else rows[-1][0]
+        inside = [min(rows, key=lambda r: abs(r[0] - mid))]
+        note = "timed region shorter than the sampling interval: the sample nearest its middle"
+    out = {"sm_mhz": float(np.median([r[1] for r in inside])), "sm_max_mhz": float(max(r[2] for r in inside)),
+           "reasons": sorted({nm for r in inside for nm in r[3]}), "samples": len(inside) if note is None else 0,
+           "interval_ms": Clocks.INTERVAL_MS}
+    if note:
+        out["note"] = note
+    return out
 
 
 def max_over_ranks(x, device):
@@ -364,6 +392,7 @@ def main():
     if world_size > 1:
         torch.distributed.barrier()
     clocks = Clocks(local_rank)
+    clocks.start()
     total_ms = 0.0
     rebuild_ms = []
     cells_total = 0

@@ -54,3 +54,27 @@ def test_reference_arm_only_on_rank0(monkeypatch):
     with contextlib.redirect_stdout(buf):
         bench.run_reference(type("A", (), dict(steps=1, warmup=0))())
     assert buf.getvalue() == ""
+
+
+def test_clock_summary_keeps_the_timed_region():
+    """Only samples stamped inside the timed region count; a throttle reason outside it is not
+    reported; a region between two samples takes the nearest one and says so."""
+    import datetime
+
+    base = datetime.datetime(2026, 1, 2, 3, 4, 5)
+
+    def line(dt_s, sm, reason=""):
+        ts = (base + datetime.timedelta(seconds=dt_s)).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        flags = ["Active" if reason == nm else "Not Active"
+                 for nm in ("hw", "hw_thermal", "sw_thermal", "sw_power_cap")]
+        return f"{ts}, 0, {sm} MHz, 2070 MHz, 900.00 W, 0x0, " + ", ".join(flags)
+
+    lines = [line(0.0, 1200, "hw"), line(0.05, 2070), line(0.10, 2070, "sw_power_cap"), line(0.15, 2055),
+             line(0.20, 1500, "hw_thermal"), "garbage"]
+    t = lambda s: (base + datetime.timedelta(seconds=s)).timestamp()  # noqa: E731
+    c = bench.summarise_clocks(lines, t(0.04), t(0.16))
+    assert c["samples"] == 3 and c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"]
+    c = bench.summarise_clocks(lines, t(0.16), t(0.17))
+    assert c["samples"] == 0 and c["sm_mhz"] == 2055.0 and "note" in c
+    assert bench.summarise_clocks([], t(0), t(1))["reasons"] == ["no samples"]
