@@ -96,6 +96,8 @@ def parse():
                     help="run three forward and three backward pose queries of 1,048,576 poses only")
     ap.add_argument("--profile-surrogate", action="store_true",
                     help="run five surrogate inferences (with the exact fallback) of the 400x400x72 map only")
+    ap.add_argument("--profile-sdf", action="store_true",
+                    help="three SDFs of the 400x400x72 risk grid and nothing else (for ncu)")
     ap.add_argument("--profile-rebuild", action="store_true",
                     help="only run three full rebuilds of the map (a short program for ncu)")
     return ap.parse_args()
@@ -334,10 +336,32 @@ def profile_rebuild():
     torch.cuda.synchronize()
 
 
+def profile_sdf():
+    """Three signed distance fields of the 400x400x72 fractal map's risk channel (obstacles
+    risk >= 1, clamp 2 m) after one rebuild: the program ncu captures."""
+    import torch
+
+    import paper_2503_02412_gb300 as seb
+    from paper_2503_02412_gb300 import abi
+    from synthetic import fractal_steps_nan
+
+    m = seb.SebMap(seb.SebParams(nx=NX, ny=NY, n_yaw=K, res=RES, length=LENGTH, width=WIDTH))
+    m.update(torch.from_numpy(fractal_steps_nan(0)).cuda())
+    risk = seb.SE2Grid.from_map(m, 4)
+    out = torch.empty((K, NY, NX), device="cuda")
+    work = torch.empty(abi.seb_sdf_workspace_bytes(NX, NY, K), dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        seb.risk_sdf(risk, 1.0, 2.0, out=out, work=work)
+    m.check()
+    torch.cuda.synchronize()
+
+
 def main():
     args = parse()
     if args.profile_rebuild:
         return profile_rebuild()
+    if args.profile_sdf:
+        return profile_sdf()
     if args.profile_surrogate:
         return profile_surrogate()
     if args.profile_query:
