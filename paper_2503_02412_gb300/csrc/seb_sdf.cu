@@ -194,6 +194,88 @@ __global__ void __launch_bounds__(kRowThreads) rows_kernel(const SdfArgs A, int 
   }
 }
 
+// Packed form of the row pass for search bounds W <= kW16Max: every squared distance, capped
+// at W^2 + 1 ("nothing within W"), fits in 16 bits, and so does every candidate, because
+// W^2 + 1 + (W + 3)^2 < 2^16.  Two candidates then share a register: one packed add and one
+// min.u16x2 (native from sm_90) handle two offsets, which halves the integer work and the
+// shared loads of the search, the pass's limit (it is issue-bound).
+//
+// Shared memory per block, for each of the two rows (distances to obstacles, to free cells):
+// four u16 copies of the row padded by P = W + 4 cap values on both sides, each Lc long (the
+// slots past the padding are never read):
+//   F_c[x + P + c] = h[x]            (c = 0, 1: forward, shifted by c)
+//   R_c[(nx - 1 - x) + P + c] = h[x] (reversed, shifted by c)
+// A cell j takes the copies whose parity makes its pairs 4-byte aligned: at offset s (odd),
+// the u32 at F_cR[j + s + P + cR] is (h[j + s], h[j + s + 1]) and the u32 at
+// R_cL[nx - 1 - j + s + P + cL] is (h[j - s], h[j - s - 1]), already paired offset by offset.
+// qtab[g] (s = 1 + 4 g) holds the packed squared offsets ((s)^2, (s+1)^2), ((s+2)^2, (s+3)^2)
+// and (s^2, s^2) for the termination test; its last entry ends every search.
+constexpr int kW16Max = 179;
+
+__device__ __forceinline__ uint32_t vmin_u16x2(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+__global__ void __launch_bounds__(kRowThreads) rows16_kernel(const SdfArgs A, int P, int Lc, int G) {
+  seb::pdl_entry();
+  extern __shared__ uint4 smem16[];
+  uint4* qtab = smem16;                                         // G + 1 entries
+  uint16_t* rows = reinterpret_cast<uint16_t*>(smem16 + G + 1);  // [2 rows][4 copies][Lc]
+  const int k = blockIdx.x / A.ny, i = blockIdx.x - k * A.ny;
+  const int nx = A.nx;
+  const uint32_t cap = (uint32_t)(A.W * A.W + 1);
+  const uint32_t* row = A.work + ((int64_t)k * A.ny + i) * nx;
+  for (int g = threadIdx.x; g <= G; g += blockDim.x) {
+    const uint32_t s = 1 + 4 * (uint32_t)g;
+    const uint32_t s1 = s + 1, s2 = s + 2, s3 = s + 3;
+    qtab[g] = g < G ? make_uint4(s * s | (s1 * s1) << 16, s2 * s2 | (s3 * s3) << 16, s * s * 0x10001u, 0u)
+                    : make_uint4(0u, 0u, 0xFFFFFFFFu, 0u);
+  }
+  for (int x = (int)threadIdx.x - P; x < nx + P; x += blockDim.x) {
+    uint32_t o = cap, f = cap;
+    if (x >= 0 && x < nx) {
+      const uint32_t v = row[x];
+      const uint32_t uo = v >> 16, uf = v & 0xFFFFu;
+      if (uo != kNone) o = uo * uo;  // column distances are <= W when not kNone
+      if (uf != kNone) f = uf * uf;
+    }
+    const int pf = x + P, pr = nx - 1 - x + P;
+    uint16_t* ro = rows;
+    uint16_t* rf = rows + (size_t)4 * Lc;
+    ro[pf] = (uint16_t)o;
+    ro[Lc + pf + 1] = (uint16_t)o;
+    ro[2 * Lc + pr] = (uint16_t)o;
+    ro[3 * Lc + pr + 1] = (uint16_t)o;
+    rf[pf] = (uint16_t)f;
+    rf[Lc + pf + 1] = (uint16_t)f;
+    rf[2 * Lc + pr] = (uint16_t)f;
+    rf[3 * Lc + pr + 1] = (uint16_t)f;
+  }
+  __syncthreads();
+  const int32_t W2 = A.W * A.W;
+  for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+    const bool obst = rows[j + P] == 0;
+    const uint16_t* h = rows + (obst ? (size_t)4 * Lc : 0);  // obstacle cells search the free cells
+    const int cR = (j + 1 + P) & 1, cL = (nx - j + P) & 1;
+    const uint32_t* pr = reinterpret_cast<const uint32_t*>(h + (size_t)cR * Lc) + ((j + 1 + P + cR) >> 1);
+    const uint32_t* pl = reinterpret_cast<const uint32_t*>(h + (size_t)(2 + cL) * Lc) + ((nx - j + P + cL) >> 1);
+    uint32_t B = (uint32_t)h[j + P] * 0x10001u;
+    for (const uint4* q = qtab;; ++q, pr += 2, pl += 2) {
+      const uint4 Q = *q;
+      if (vmin_u16x2(B, Q.z) != Q.z) break;  // a half below s^2: every farther offset costs more
+      const uint32_t a = vmin_u16x2(pr[0], pl[0]) + Q.x;
+      const uint32_t b = vmin_u16x2(pr[1], pl[1]) + Q.y;
+      B = vmin_u16x2(B, vmin_u16x2(a, b));
+    }
+    const int32_t best = (int32_t)min(B & 0xFFFFu, B >> 16);
+    float d = best > W2 ? INFINITY : A.res * sqrtf((float)best);
+    d = fminf(d, A.clamp);
+    A.sdf[phys(A, k, i, j)] = obst ? -d : d;
+  }
+}
+
 }  // namespace
 
 extern "C" size_t seb_sdf_workspace_bytes(int32_t nx, int32_t ny, int32_t n_yaw) {
@@ -248,6 +330,25 @@ extern "C" int seb_risk_sdf(const seb_grid* g, float risk_obstacle, float clamp,
   const dim3 cgrid((unsigned)((A.nx + 31) / 32), (unsigned)A.K);
   cudaError_t e = (int64_t)cgrid.x * cgrid.y < 600 ? seb::launch_pdl(cols_kernel<16>, cgrid, dim3(32 * 16), 0, st, A)
                                                   : seb::launch_pdl(cols_kernel<8>, cgrid, dim3(32 * 8), 0, st, A);
+  // packed row pass when every candidate fits in 16 bits and its rows fit in shared memory
+  // Lc = 32 (mod 64) u16: a copy and its shifted twin start 16 banks apart, so the pair loads
+  // of 32 consecutive cells (alternating between the two) hit 32 distinct banks
+  const int P16 = A.W + 4, Lc = (A.nx + 2 * P16 + 2 + 63) / 64 * 64 + 32, G = (A.W - 1) / 4 + 1;
+  const size_t smem16 = (size_t)(G + 1) * sizeof(uint4) + (size_t)8 * Lc * sizeof(uint16_t);
+  if (e == cudaSuccess && A.W <= kW16Max && smem16 <= kPadSmemMax) {
+    e = cudaFuncSetAttribute(rows16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem16);
+    if (e == cudaSuccess) {
+      const int passes = (A.nx + kRowThreads - 1) / kRowThreads;
+      const int rthreads = ((A.nx + passes - 1) / passes + 31) / 32 * 32;
+      e = seb::launch_pdl(rows16_kernel, dim3((unsigned)((int64_t)A.K * A.ny)), dim3(rthreads), smem16, st, A,
+                          P16, Lc, G);
+    }
+    if (e != cudaSuccess) {
+      seb::set_error("seb_risk_sdf launch: %s", cudaGetErrorString(e));
+      return SEB_ERR_CUDA;
+    }
+    return SEB_OK;
+  }
   // padding of the row pass: the search reaches offset min(W, nx - 1) + 3
   const int P = min(A.W, A.nx - 1) + 4;
   const size_t psmem = (size_t)2 * (A.nx + 2 * (size_t)P) * sizeof(int32_t);

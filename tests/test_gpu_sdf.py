@@ -98,3 +98,23 @@ def test_sdf_grid_lookup(seb):
     poses = torch.from_numpy(lookup_poses(12, 1000, 40, 30, RES, (-4, 9), pad_cells=0.0)).cuda()
     val, grad, fl = seb.se2_lookup(s, poses, with_grad=True)
     assert (fl == 0).all() and torch.isfinite(val).all() and (val.abs() <= 1.0).all()
+
+
+@pytest.mark.parametrize("clamp", [8.875, 8.925, math.inf])
+def test_packed_and_padded_row_passes(seb, clamp):
+    """The row pass packs two candidates per register while the search bound W = ceil(clamp /
+    res) + 1 is at most 179 (W = 179 here) and keeps 32-bit candidates above (W = 180, and W =
+    the row length without a clamp); sparse obstacles on 420-column rows make the searches run
+    to the bound.  Sampled cells against the FP64 reference."""
+    K, ny, nx = 2, 24, 420
+    risk = obstacle_risk(43, K, ny, nx, n_blobs=2, blob_cells=(1, 3))
+    got = gpu_sdf(seb, risk, ring=(17, 5), clamp=clamp)._owner.cpu().numpy()
+    rng = np.random.default_rng(44)
+    m = 2500
+    cells = np.stack([rng.integers(0, nx, m), rng.integers(0, ny, m), rng.integers(0, K, m)], 1)
+    ref = ref_sdf(risk.astype(np.float64), RES_F, clamp=clamp, ring=(17, 5), cells=cells)
+    g = got[cells[:, 2], (cells[:, 1] + 5) % ny, (cells[:, 0] + 17) % nx]
+    fin = np.isfinite(ref)
+    assert np.abs(ref[fin]).max() > 5.0  # long searches
+    assert np.array_equal(np.isfinite(g), fin)
+    assert np.abs(g[fin] - ref[fin]).max() <= TOL * max(1.0, np.abs(ref[fin]).max())
