@@ -19,7 +19,8 @@
 //   2. rows_kernel: a block per (bin, row) stages that row's squared column distances in shared
 //      memory, padded with "no feature" sentinels; every cell takes the minimum of
 //      g(j')^2 + (j - j')^2 over |j - j'| = 0, 1, 2, ..., four offsets per step, and stops when
-//      (j - j')^2 alone reaches the best value.  The squared distances are exact 32-bit integers.
+//      (j - j')^2 alone reaches the best value.  The squared distances are exact 32-bit integers;
+//      while W <= 179, rows16_kernel runs the same search on packed 16-bit pairs.
 #include <cuda_runtime.h>
 #include <limits.h>
 #include <math.h>
@@ -198,7 +199,8 @@ __global__ void __launch_bounds__(kRowThreads) rows_kernel(const SdfArgs A, int 
 // at W^2 + 1 ("nothing within W"), fits in 16 bits, and so does every candidate, because
 // W^2 + 1 + (W + 3)^2 < 2^16.  Two candidates then share a register: one packed add and one
 // min.u16x2 (native from sm_90) handle two offsets, which halves the integer work and the
-// shared loads of the search, the pass's limit (it is issue-bound).
+// shared loads of the search (the 32-bit pass is issue-bound; this one is bound by the
+// shared-memory pipe).
 //
 // Shared memory per block, for each of the two rows (distances to obstacles, to free cells):
 // four u16 copies of the row padded by P = W + 4 cap values on both sides, each Lc long (the
