@@ -14,9 +14,8 @@
 // W = ceil(clamp / res) + 1 cells can fall under the clamp, so W bounds both passes.
 //   1. cols_kernel: sweeps every column down and up (linear time), split in 8 row segments (16 on
 //      small grids) swept by separate warps and joined through their first / last obstacle and
-//      free rows, and stores per cell the distance in rows to the nearest obstacle and to the
-//      nearest free cell of its column (uint16 each, 0xFFFF = none within W).  Loads are issued
-//      8 rows at a time; on large grids each lane sweeps two columns, 32 apart.
+//      free rows, and stores per cell the distance in rows to the nearest obstacle and to the nearest free cell
+//      of its column (uint16 each, 0xFFFF = none within W).  Loads are issued 8 rows at a time.
 //   2. rows_kernel: a block per (bin, row) stages that row's squared column distances in shared
 //      memory, padded with "no feature" sentinels; every cell takes the minimum of
 //      g(j')^2 + (j - j')^2 over |j - j'| = 0, 1, 2, ..., four offsets per step, and stops when
@@ -55,79 +54,59 @@ __device__ __forceinline__ int64_t phys(const SdfArgs& A, int k, int i, int j) {
   return ((int64_t)k * A.ny + r) * A.nx + c;
 }
 
-// SEGS row segments (warps) per column stripe: more of them when the grid has few stripes.  NC
-// columns per lane (stripes of 32 NC columns): two on large grids, which halves the block count
-// (one wave of blocks instead of two at 400x400x72) and doubles each thread's loads in flight.
-template <int SEGS, int NC>
+// SEGS row segments (warps) per column stripe: more of them when the grid has few stripes.
+template <int SEGS>
 __global__ void __launch_bounds__(32 * SEGS) cols_kernel(const SdfArgs A) {
   seb::pdl_entry();
-  // a block per (bin, stripe): lane + 32 c = column, warp = one of SEGS row segments.  Each warp
-  // sweeps its segment down (distances to the nearest obstacle / free cell at or above, within
-  // the segment) and records the segment's first and last obstacle / free rows; after a barrier
-  // it sweeps up, completing each distance with the nearest rows of the other segments.
-  __shared__ int seg_rows[SEGS][4][32 * NC];  // last obstacle, first obstacle, last free, first free
-  const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5, k = blockIdx.y;
+  // a block per (bin, 32-column stripe): lane = column, warp = one of SEGS row segments.  Each
+  // warp sweeps its segment down (distances to the nearest obstacle / free cell at or above,
+  // within the segment) and records the segment's first and last obstacle / free rows; after a
+  // barrier it sweeps up, completing each distance with the nearest rows of the other segments.
+  __shared__ int seg_rows[SEGS][4][32];  // last obstacle, first obstacle, last free, first free
+  const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane, k = blockIdx.y;
   const int L = (A.ny + SEGS - 1) / SEGS, i0 = min(A.ny, seg * L), i1 = min(A.ny, i0 + L);
-  int j[NC], last_o[NC], first_o[NC], last_f[NC], first_f[NC];
-  bool col[NC];
+  const bool col = j < A.nx;
+  uint32_t* out = A.work + (int64_t)k * A.ny * A.nx + j;
+  int last_o = -1, first_o = -1, last_f = -1, first_f = -1;
+  if (col) {
+    // kBatch loads in flight before the batch's stores (the stores could alias the loads)
+    for (int ib = i0; ib < i1; ib += kBatch) {
+      float v[kBatch];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    j[c] = blockIdx.x * 32 * NC + 32 * c + lane;
-    col[c] = j[c] < A.nx;
-    last_o[c] = first_o[c] = last_f[c] = first_f[c] = -1;
-  }
-  uint32_t* out = A.work + (int64_t)k * A.ny * A.nx;
-  // kBatch loads per column in flight before the batch's stores (the stores could alias the loads)
-  for (int ib = i0; ib < i1; ib += kBatch) {
-    float v[NC][kBatch];
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u)
-        v[c][u] = col[c] && ib + u < i1 ? __ldg(A.risk + phys(A, k, ib + u, j[c])) : 0.f;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      if (!col[c]) continue;
+      for (int u = 0; u < kBatch; ++u) v[u] = ib + u < i1 ? __ldg(A.risk + phys(A, k, ib + u, j)) : 0.f;
 #pragma unroll
       for (int u = 0; u < kBatch; ++u) {
         const int i = ib + u;
         if (i >= i1) break;
-        const bool ob = !(v[c][u] < A.thr);  // NaN: obstacle
+        const bool ob = !(v[u] < A.thr);  // NaN: obstacle
         if (ob) {
-          last_o[c] = i;
-          first_o[c] = first_o[c] < 0 ? i : first_o[c];
+          last_o = i;
+          first_o = first_o < 0 ? i : first_o;
         } else {
-          last_f[c] = i;
-          first_f[c] = first_f[c] < 0 ? i : first_f[c];
+          last_f = i;
+          first_f = first_f < 0 ? i : first_f;
         }
-        const uint32_t uo = last_o[c] < 0 ? kNone : (uint32_t)(i - last_o[c]);
-        const uint32_t uf = last_f[c] < 0 ? kNone : (uint32_t)(i - last_f[c]);
-        out[(int64_t)i * A.nx + j[c]] = (uo << 16) | uf;
+        const uint32_t uo = last_o < 0 ? kNone : (uint32_t)(i - last_o);
+        const uint32_t uf = last_f < 0 ? kNone : (uint32_t)(i - last_f);
+        out[(int64_t)i * A.nx] = (uo << 16) | uf;
       }
     }
   }
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    seg_rows[seg][0][32 * c + lane] = last_o[c];
-    seg_rows[seg][1][32 * c + lane] = first_o[c];
-    seg_rows[seg][2][32 * c + lane] = last_f[c];
-    seg_rows[seg][3][32 * c + lane] = first_f[c];
-  }
+  seg_rows[seg][0][lane] = last_o;
+  seg_rows[seg][1][lane] = first_o;
+  seg_rows[seg][2][lane] = last_f;
+  seg_rows[seg][3][lane] = first_f;
   __syncthreads();
-  int above_o[NC], above_f[NC], next_o[NC], next_f[NC];
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    const int t = 32 * c + lane;
-    above_o[c] = above_f[c] = -1;
-    next_o[c] = next_f[c] = INT_MAX;
-    for (int s2 = seg - 1; s2 >= 0; --s2) {
-      if (above_o[c] < 0) above_o[c] = seg_rows[s2][0][t];
-      if (above_f[c] < 0) above_f[c] = seg_rows[s2][2][t];
-    }
-    for (int s2 = seg + 1; s2 < SEGS; ++s2) {
-      if (next_o[c] == INT_MAX && seg_rows[s2][1][t] >= 0) next_o[c] = seg_rows[s2][1][t];
-      if (next_f[c] == INT_MAX && seg_rows[s2][3][t] >= 0) next_f[c] = seg_rows[s2][3][t];
-    }
+  if (!col) return;
+  int above_o = -1, above_f = -1, next_o = INT_MAX, next_f = INT_MAX;
+  for (int s2 = seg - 1; s2 >= 0; --s2) {
+    if (above_o < 0) above_o = seg_rows[s2][0][lane];
+    if (above_f < 0) above_f = seg_rows[s2][2][lane];
+  }
+  for (int s2 = seg + 1; s2 < SEGS; ++s2) {
+    if (next_o == INT_MAX && seg_rows[s2][1][lane] >= 0) next_o = seg_rows[s2][1][lane];
+    if (next_f == INT_MAX && seg_rows[s2][3][lane] >= 0) next_f = seg_rows[s2][3][lane];
   }
   const int W = A.W;
   auto fin = [&](uint32_t up_in_seg, int above, int next, int i) -> uint32_t {
@@ -136,24 +115,17 @@ __global__ void __launch_bounds__(32 * SEGS) cols_kernel(const SdfArgs A) {
     return d > W ? kNone : (uint32_t)d;
   };
   for (int ib = i1 - 1; ib >= i0; ib -= kBatch) {
-    uint32_t w[NC][kBatch];
+    uint32_t w[kBatch];
 #pragma unroll
-    for (int c = 0; c < NC; ++c)
+    for (int u = 0; u < kBatch; ++u) w[u] = ib - u >= i0 ? out[(int64_t)(ib - u) * A.nx] : 0u;
 #pragma unroll
-      for (int u = 0; u < kBatch; ++u) w[c][u] = col[c] && ib - u >= i0 ? out[(int64_t)(ib - u) * A.nx + j[c]] : 0u;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      if (!col[c]) continue;
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        const int i = ib - u;
-        if (i < i0) break;
-        const uint32_t uo = w[c][u] >> 16, uf = w[c][u] & 0xFFFFu;
-        if (uo == 0) next_o[c] = i;
-        if (uf == 0) next_f[c] = i;
-        out[(int64_t)i * A.nx + j[c]] =
-            (fin(uo, above_o[c], next_o[c], i) << 16) | fin(uf, above_f[c], next_f[c], i);
-      }
+    for (int u = 0; u < kBatch; ++u) {
+      const int i = ib - u;
+      if (i < i0) break;
+      const uint32_t uo = w[u] >> 16, uf = w[u] & 0xFFFFu;
+      if (uo == 0) next_o = i;
+      if (uf == 0) next_f = i;
+      out[(int64_t)i * A.nx] = (fin(uo, above_o, next_o, i) << 16) | fin(uf, above_f, next_f, i);
     }
   }
 }
@@ -356,13 +328,10 @@ extern "C" int seb_risk_sdf(const seb_grid* g, float risk_obstacle, float clamp,
   if (!(w < side)) w = side;
   A.W = (int)w;
   const cudaStream_t st = (cudaStream_t)stream;
-  // 16 row segments per 32-column stripe when the grid has few stripes (a small map), else 8
-  // segments per 64-column stripe
+  // 16 row segments per stripe when the grid has few stripes (a small map), else 8
   const dim3 cgrid((unsigned)((A.nx + 31) / 32), (unsigned)A.K);
-  const dim3 cgrid2((unsigned)((A.nx + 63) / 64), (unsigned)A.K);
-  cudaError_t e = (int64_t)cgrid.x * cgrid.y < 600
-                      ? seb::launch_pdl(cols_kernel<16, 1>, cgrid, dim3(32 * 16), 0, st, A)
-                      : seb::launch_pdl(cols_kernel<8, 2>, cgrid2, dim3(32 * 8), 0, st, A);
+  cudaError_t e = (int64_t)cgrid.x * cgrid.y < 600 ? seb::launch_pdl(cols_kernel<16>, cgrid, dim3(32 * 16), 0, st, A)
+                                                  : seb::launch_pdl(cols_kernel<8>, cgrid, dim3(32 * 8), 0, st, A);
   // packed row pass when every candidate fits in 16 bits and its rows fit in shared memory
   // Lc = 32 (mod 64) u16: a copy and its shifted twin start 16 banks apart, so the pair loads
   // of 32 consecutive cells (alternating between the two) hit 32 distinct banks

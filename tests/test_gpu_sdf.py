@@ -36,8 +36,8 @@ def gpu_sdf(seb, risk_np, ring=(0, 0), origin=(0, 0), **kw):
                                         ((2, 64, 64), (63, 63)), ((150, 12, 130), (77, 5))])
 def test_full_grid_parity(seb, shape, ring):
     """Every cell against the FP64 reference.  The last grid has enough 32-column stripes x bins
-    (750) for the column pass's two-columns-per-lane form, with a ragged last stripe (130 =
-    2 x 64 + 2 columns)."""
+    (750) for the large-grid column pass (8 row segments per stripe), with a ragged last stripe
+    (130 = 4 x 32 + 2 columns)."""
     K, ny, nx = shape
     risk = obstacle_risk(7, K, ny, nx, n_blobs=4, blob_cells=(1, 6))
     ring = (ring[0] % nx, ring[1] % ny)
