@@ -107,3 +107,36 @@ def test_footprint_table_bad_args(lib):
     assert lib.seb_footprint_table(None, 0, None, None, 0) == abi.SEB_ERR_INVALID_ARG
     p.length = 30.0  # reach beyond the 127-cell packing
     assert lib.seb_footprint_table(ctypes.byref(p), 0, None, None, 0) == abi.SEB_ERR_BAD_SHAPE
+
+
+def test_sdf_inpaint_and_batch_argument_checks_without_gpu(lib):
+    """Argument checks that return before any CUDA call: NULL and out-of-range arguments, an
+    undersized workspace, an output aliasing its input, a negative clamp, a negative batch."""
+    import ctypes
+
+    nx, ny, K = 400, 400, 72
+    assert lib.seb_sdf_workspace_bytes(nx, ny, K) == nx * ny * K * 4
+    assert lib.seb_sdf_workspace_bytes(0, ny, K) == 0 and lib.seb_sdf_workspace_bytes(nx, 16385, K) == 0
+    assert lib.seb_inpaint_workspace_bytes(nx, ny) == nx * ny * 4 and lib.seb_inpaint_workspace_bytes(nx, 0) == 0
+    fake = 0x100000  # never dereferenced: every call below fails its checks first
+    g = abi.seb_grid(data=fake, nx=nx, ny=ny, n_yaw=K, ring_x=0, ring_y=0, origin_i=0, origin_j=0, res=0.05)
+    need = nx * ny * K * 4
+    sdf = lib.seb_risk_sdf
+    assert sdf(None, 1.0, 2.0, fake, need, 0x200000, None) == abi.SEB_ERR_INVALID_ARG
+    assert sdf(ctypes.byref(g), 1.0, 2.0, fake, need, None, None) == abi.SEB_ERR_INVALID_ARG
+    assert sdf(ctypes.byref(g), 1.0, -1.0, 0x300000, need, 0x200000, None) == abi.SEB_ERR_INVALID_ARG
+    assert sdf(ctypes.byref(g), 1.0, 2.0, 0x300000, need - 4, 0x200000, None) == abi.SEB_ERR_WORKSPACE
+    assert sdf(ctypes.byref(g), 1.0, 2.0, 0x300001, need, 0x200000, None) == abi.SEB_ERR_WORKSPACE
+    assert sdf(ctypes.byref(g), 1.0, 2.0, 0x300000, need, fake, None) == abi.SEB_ERR_INVALID_ARG  # aliasing
+    for bad in (dict(nx=0), dict(ring_x=nx), dict(ring_y=-1), dict(res=0.0), dict(n_yaw=0)):
+        gb = abi.seb_grid(data=fake, nx=nx, ny=ny, n_yaw=K, ring_x=0, ring_y=0, origin_i=0, origin_j=0, res=0.05)
+        for k, v in bad.items():
+            setattr(gb, k, v)
+        assert sdf(ctypes.byref(gb), 1.0, 2.0, 0x300000, need, 0x200000, None) == abi.SEB_ERR_BAD_SHAPE, bad
+    inp = lib.seb_inpaint_nearest
+    wneed = nx * ny * 4
+    assert inp(None, nx, ny, 0, 0x300000, wneed, 0x200000, None, None) == abi.SEB_ERR_INVALID_ARG
+    assert inp(fake, 0, ny, 0, 0x300000, wneed, 0x200000, None, None) == abi.SEB_ERR_BAD_SHAPE
+    assert inp(fake, nx, ny, 0, 0x300000, wneed, fake, None, None) == abi.SEB_ERR_INVALID_ARG
+    assert inp(fake, nx, ny, 0, 0x300000, wneed - 1, 0x200000, None, None) == abi.SEB_ERR_WORKSPACE
+    assert lib.seb_map_shift_batch(None, None, None, 0) == abi.SEB_ERR_INVALID_ARG
