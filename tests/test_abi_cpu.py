@@ -140,3 +140,60 @@ def test_sdf_inpaint_and_batch_argument_checks_without_gpu(lib):
     assert inp(fake, nx, ny, 0, 0x300000, wneed, fake, None, None) == abi.SEB_ERR_INVALID_ARG
     assert inp(fake, nx, ny, 0, 0x300000, wneed - 1, 0x200000, None, None) == abi.SEB_ERR_WORKSPACE
     assert lib.seb_map_shift_batch(None, None, None, 0) == abi.SEB_ERR_INVALID_ARG
+
+
+def test_handle_and_shape_checks_without_gpu(lib):
+    """NULL handles, bad grid shapes, negative counts and bad elevation-map parameters are
+    rejected with their status codes before any CUDA call."""
+    import ctypes
+
+    INV, SHAPE, WS = abi.SEB_ERR_INVALID_ARG, abi.SEB_ERR_BAD_SHAPE, abi.SEB_ERR_WORKSPACE
+    fake = 0x100000  # never dereferenced
+    # rolling map entry points with no map
+    assert lib.seb_map_set_stream(None, None) == INV
+    assert lib.seb_map_update(None, fake, 0, 0) == INV
+    assert lib.seb_map_shift(None, fake, 0, 0) == INV
+    assert lib.seb_map_view(None, ctypes.byref(abi.seb_view())) == INV
+    assert lib.seb_map_copy_out(None, fake, fake) == INV
+    assert lib.seb_map_check(None, 10, None, None) == INV
+    assert lib.seb_map_grid(None, 0, ctypes.byref(abi.seb_grid())) == INV
+    # trilinear lookup: grid checks, then counts and pointers
+    good = dict(data=fake, nx=40, ny=30, n_yaw=36, ring_x=0, ring_y=0, origin_i=0, origin_j=0, res=0.1)
+    assert lib.seb_se2_lookup(None, fake, 1, 0.0, fake, None, None, None) == INV
+    for bad in (dict(data=None), dict(nx=1), dict(ny=1), dict(n_yaw=0), dict(n_yaw=4097), dict(res=0.0),
+                dict(res=float("inf")), dict(ring_x=40), dict(ring_y=-1)):
+        g = abi.seb_grid(**dict(good, **bad))
+        want = INV if "data" in bad else SHAPE
+        assert lib.seb_se2_lookup(ctypes.byref(g), fake, 1, 0.0, fake, None, None, None) == want, bad
+        assert lib.seb_se2_lookup_vjp(ctypes.byref(g), fake, 1, fake, fake, None) == want, bad
+    g = abi.seb_grid(**good)
+    assert lib.seb_se2_lookup(ctypes.byref(g), fake, -1, 0.0, fake, None, None, None) == INV
+    assert lib.seb_se2_lookup(ctypes.byref(g), None, 5, 0.0, fake, None, None, None) == INV
+    assert lib.seb_se2_lookup_vjp(ctypes.byref(g), fake, 5, fake, None, None) == INV
+    # allocation-free pose query
+    p = abi.seb_params_default()
+    assert lib.seb_query_poses_grad_noalloc(ctypes.byref(p), None, 0, 0, fake, 1, fake, fake, fake, fake, None) == INV
+    assert lib.seb_query_poses_grad_noalloc(ctypes.byref(p), fake, 0, 0, fake, -1, fake, fake, fake, fake, None) == INV
+    # elevation map: parameters, workspace size, handles
+    ep = abi.seb_elev_params()
+    lib.seb_elev_params_default(ctypes.byref(ep))
+    assert (ep.nx, ep.ny) == (400, 400) and abs(ep.res - 0.05) < 1e-7 and ep.z_min < ep.z_max and ep.gate > 0
+    n = lib.seb_elev_workspace_bytes(ctypes.byref(ep), 1000)
+    assert n > 0 and lib.seb_elev_workspace_bytes(ctypes.byref(ep), 2000) > n
+    assert lib.seb_elev_workspace_bytes(ctypes.byref(ep), -1) == 0
+    h = ctypes.c_void_p()
+    assert lib.seb_elev_create(ctypes.byref(ep), 1000, fake, n, None, None) == INV
+    assert lib.seb_elev_create(ctypes.byref(ep), 1000, None, n, None, ctypes.byref(h)) == WS
+    assert lib.seb_elev_create(ctypes.byref(ep), 1000, fake + 16, n, None, ctypes.byref(h)) == WS  # not 256-aligned
+    assert lib.seb_elev_create(ctypes.byref(ep), 1000, fake, n - 1, None, ctypes.byref(h)) == WS
+    for field, value in (("nx", 0), ("ny", 16385), ("res", 0.0), ("res", float("nan")), ("gate", 0.0), ("z_min", 2.0)):
+        bad = abi.seb_elev_params()
+        lib.seb_elev_params_default(ctypes.byref(bad))
+        setattr(bad, field, value)
+        assert lib.seb_elev_workspace_bytes(ctypes.byref(bad), 10) == 0, field
+        assert lib.seb_elev_create(ctypes.byref(bad), 10, fake, 1 << 30, None, ctypes.byref(h)) == INV, field
+    assert lib.seb_elev_set_stream(None, None) == INV
+    assert lib.seb_elev_integrate(None, ctypes.byref(abi.seb_scan_pose()), fake, 1) == INV
+    assert lib.seb_elev_view_get(None, ctypes.byref(abi.seb_elev_view())) == INV
+    assert lib.seb_elev_copy_out(None, fake, fake) == INV
+    assert lib.seb_elev_destroy(None) == abi.SEB_OK
