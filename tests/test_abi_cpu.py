@@ -197,3 +197,43 @@ def test_handle_and_shape_checks_without_gpu(lib):
     assert lib.seb_elev_view_get(None, ctypes.byref(abi.seb_elev_view())) == INV
     assert lib.seb_elev_copy_out(None, fake, fake) == INV
     assert lib.seb_elev_destroy(None) == abi.SEB_OK
+
+
+def test_surrogate_argument_checks_without_gpu(lib):
+    """The surrogate's entry points reject NULL handles, bad batches and engines, maps smaller
+    than the network's 33 x 33 window, non-FP32 elevation and bad workspaces before any CUDA
+    call."""
+    import ctypes
+
+    INV, WS = abi.SEB_ERR_INVALID_ARG, abi.SEB_ERR_WORKSPACE
+    fake = 0x100000  # never dereferenced
+    p = abi.seb_params_default()
+    p.nx = p.ny = 200
+    p.n_yaw = 72
+    p.res = 0.05
+    n = lib.seb_sur_workspace_bytes(ctypes.byref(p), 8)
+    assert n > 0 and lib.seb_sur_workspace_bytes(ctypes.byref(p), 16) > n
+    assert lib.seb_sur_workspace_bytes(ctypes.byref(p), 0) == 0 and lib.seb_sur_workspace_bytes(None, 8) == 0
+    h = ctypes.c_void_p()
+    assert lib.seb_sur_create(None, 8, fake, n, None, ctypes.byref(h)) == INV
+    assert lib.seb_sur_create(ctypes.byref(p), 0, fake, n, None, ctypes.byref(h)) == INV
+    assert lib.seb_sur_create(ctypes.byref(p), 8, fake, n, None, None) == INV
+    assert lib.seb_sur_create(ctypes.byref(p), 8, None, n, None, ctypes.byref(h)) == WS
+    assert lib.seb_sur_create(ctypes.byref(p), 8, fake + 64, n, None, ctypes.byref(h)) == WS  # not 256-aligned
+    assert lib.seb_sur_create(ctypes.byref(p), 8, fake, n - 1, None, ctypes.byref(h)) == WS
+    small = abi.seb_params_default()
+    small.nx = small.ny = 32
+    assert lib.seb_sur_create(ctypes.byref(small), 8, fake, 1 << 34, None, ctypes.byref(h)) == INV
+    half = abi.seb_params_default()
+    half.nx = half.ny = 200
+    half.elev_dtype = abi.SEB_BF16
+    assert lib.seb_sur_create(ctypes.byref(half), 8, fake, 1 << 34, None, ctypes.byref(h)) == INV
+    assert lib.seb_sur_destroy(None) == INV
+    assert lib.seb_sur_set_stream(None, None) == INV
+    assert lib.seb_sur_set_engine(None, abi.SEB_SUR_SIMT) == INV
+    assert lib.seb_sur_view_get(None, ctypes.byref(abi.seb_sur_view())) == INV
+    assert lib.seb_sur_init(None, 1) == INV
+    assert lib.seb_sur_gather(None, fake, fake, 200, 200, fake, 1, 0) == INV
+    assert lib.seb_sur_forward(None, 1) == INV
+    assert lib.seb_sur_train_step(None, 1, 1e-3, 1, None) == INV
+    assert lib.seb_sur_infer(None, fake, 0.04, 3, 1, fake, fake, None) == INV
