@@ -237,3 +237,13 @@ def test_surrogate_argument_checks_without_gpu(lib):
     assert lib.seb_sur_forward(None, 1) == INV
     assert lib.seb_sur_train_step(None, 1, 1e-3, 1, None) == INV
     assert lib.seb_sur_infer(None, fake, 0.04, 3, 1, fake, fake, None) == INV
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libseb.so the binding raises at first use; nothing falls back to a CPU path."""
+    monkeypatch.setattr(abi, "_lib", None)
+    monkeypatch.setattr(abi, "LIB_PATH", str(tmp_path / "libseb.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        abi.load()
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        abi.seb_params_default()
