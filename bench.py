@@ -261,7 +261,7 @@ def run_reference(args):
         return
     world, origins = workload()
     per_step = max(1.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
-    cb = cpu_baseline(world, origins, per_step * 4)
+    cb = cpu_baseline(world, origins, min(5.0, per_step * 4))  # sizes the steps only
     import oracle
 
     p = oracle_params()
