@@ -421,6 +421,26 @@ int seb_sur_forward(seb_sur* h, int32_t batch);
  */
 int seb_sur_infer(seb_sur* h, const float* elev_dev, float step, int32_t radius, int32_t exact_fallback,
                   float* out_dev, uint8_t* flags_dev, uint8_t* mask_dev);
+/*
+ * Checkpoint / resume of training (the paper has no learned model; this serves the surrogate
+ * above).  The image holds everything the training step carries from one call to the next: the
+ * FP32 master weights, the Adam first and second moments, the BF16 weights the kernels read and
+ * the Adam step of the last seb_sur_train_step, behind a 64-byte header that names the network's
+ * size.  Training itself draws no random numbers (the caller seeds seb_terrain_bumpy and picks
+ * the patch centres), and its reductions run in a fixed order, so a run resumed from an image
+ * with the caller's own generator state restored repeats the original run bit for bit.
+ *   seb_sur_state_bytes: size of the image (0 for NULL).
+ *   seb_sur_save: writes the image to caller-owned HOST memory host_dst (>= that many bytes);
+ *     enqueues the copies on the handle's stream and synchronises it (a blocking call).
+ *   seb_sur_load: restores an image into a handle of the same network (same n_yaw); rejects
+ *     images of another size or without the header with SEB_ERR_INVALID_ARG; blocking.
+ *   seb_sur_step: the Adam step of the last train step (0 after init, the saved step after a
+ *     load), -1 for NULL.
+ */
+size_t seb_sur_state_bytes(const seb_sur* h);
+int seb_sur_save(seb_sur* h, void* host_dst, size_t bytes);
+int seb_sur_load(seb_sur* h, const void* host_src, size_t bytes);
+int64_t seb_sur_step(const seb_sur* h);
 /* Terrain of the small-map recipe on the GPU (training data): per world 36 parameters
  * (tan slope, azimuth, noise sigma, unused, then (amplitude, sigma, cx, cy) x 8 bumps); the
  * noise is N(0, sigma) from a counter-based generator seeded by seed.  out_dev [n][ny][nx]. */
@@ -438,10 +458,16 @@ int seb_terrain_bumpy(const float* params_dev, int32_t n, int32_t nx, int32_t ny
  *   poses_dev [n][3], grad_out_dev [n][SEB_N_CH] (inputs); out_dev [n][SEB_N_CH],
  *   flags_dev [n], grad_pose_dev [n][3] (outputs, caller-owned).
  * n > SEB_NOALLOC_MAX_POSES returns SEB_ERR_INVALID_ARG with a message naming the limit.
- * Calls no allocating routine.  All calls share the array: calls whose kernels overlap on the
- * GPU (unordered streams) race on it; calls on one stream are safe.  Nothing in it needs
- * clearing: the forward writes every record the backward reads.  The first call on a device
- * looks the array's address up with that device current; make it before any stream capture.
+ * Parameters are validated exactly as seb_query_poses validates them (same lattice, same
+ * limits).  Calls no cudaMalloc, cudaFree or other allocating routine, and no host heap
+ * allocation either.  All calls share the array: calls whose kernels overlap on the GPU
+ * (unordered streams) race on it; calls on one stream are safe.  Nothing in it needs clearing:
+ * the forward writes every record the backward reads.  The first call on a device looks the
+ * array's address up (cudaGetSymbolAddress, with that device current); under lazy module
+ * loading that lookup is what loads the library's device code and the 4 MiB array onto the
+ * device, so it can fail for lack of device memory.  Make one warm-up call per device at
+ * start-up (n = 0 is not enough: it returns before the lookup; any n >= 1 does it), before any
+ * stream capture and before the fixed memory budget is taken.
  */
 #define SEB_NOALLOC_MAX_POSES 65536
 int seb_query_poses_grad_noalloc(const seb_params* p, const void* elev_dev, int64_t origin_i,

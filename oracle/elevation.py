@@ -29,8 +29,11 @@ order of Sec. V-A:
    the points inside the gate; an unknown cell takes the fusion of all its points.  Fusion:
    1 / s2' = [1 / s2] + sum 1 / s2_i and h' = s2' ([h / s2] + sum z_i / s2_i).
 
-Readings of the paper behind these steps are listed in the design notes; pins are in
-``tests/test_elevation_pins.py``.
+Readings of Sec. V-A behind these steps: the world height uses + p_B (a rigid transform; the
+sign reaches the variance only through J_B, which enters squared); the window is the robot's
+cell minus half the map size (Eq. (pm)); ray casting clears a crossed cell whose height exceeds
+the ray's top over it by more than clear_margin; several points in a cell are fused against the
+pre-scan estimate with the Mahalanobis gate above.  Pins are in ``tests/test_elevation_pins.py``.
 """
 from __future__ import annotations
 

@@ -75,6 +75,10 @@ EXPORTS = (
     "seb_sur_train_step",
     "seb_sur_forward",
     "seb_sur_infer",
+    "seb_sur_state_bytes",
+    "seb_sur_save",
+    "seb_sur_load",
+    "seb_sur_step",
     "seb_terrain_bumpy",
 )
 
@@ -246,6 +250,10 @@ def load():
             "seb_sur_forward": (ctypes.c_int, [vp, i32]),
             "seb_sur_infer": (ctypes.c_int, [vp, vp, ctypes.c_float, i32, i32, vp, vp, vp]),
             "seb_terrain_bumpy": (ctypes.c_int, [vp, i32, i32, i32, ctypes.c_float, ctypes.c_uint64, vp, vp]),
+            "seb_sur_state_bytes": (sz, [vp]),
+            "seb_sur_save": (ctypes.c_int, [vp, vp, sz]),
+            "seb_sur_load": (ctypes.c_int, [vp, vp, sz]),
+            "seb_sur_step": (i64, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -476,6 +484,27 @@ def seb_sur_forward(handle, batch) -> None:
 
 def seb_sur_infer(handle, elev_ptr, step, radius, exact_fallback, out_ptr, flags_ptr, mask_ptr=0) -> None:
     _check(load().seb_sur_infer(handle, elev_ptr, step, radius, exact_fallback, out_ptr, flags_ptr, mask_ptr))
+
+
+def seb_sur_state_bytes(handle) -> int:
+    return int(load().seb_sur_state_bytes(handle))
+
+
+def seb_sur_save(handle) -> bytes:
+    """Checkpoint image of the training state (blocking: synchronises the handle's stream)."""
+    n = seb_sur_state_bytes(handle)
+    buf = ctypes.create_string_buffer(n)
+    _check(load().seb_sur_save(handle, buf, n))
+    return buf.raw
+
+
+def seb_sur_load(handle, image: bytes) -> None:
+    buf = ctypes.create_string_buffer(bytes(image), len(image))
+    _check(load().seb_sur_load(handle, buf, len(image)))
+
+
+def seb_sur_step(handle) -> int:
+    return int(load().seb_sur_step(handle))
 
 
 def seb_terrain_bumpy(params_ptr, n, nx, ny, res, seed, out_ptr, stream=0) -> None:

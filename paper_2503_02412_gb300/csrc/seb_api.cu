@@ -124,6 +124,7 @@ using namespace seb;
 extern "C" {
 
 void seb_params_default(seb_params* p) {
+  SEB_RANGE();
   if (!p) return;
   memset(p, 0, sizeof(*p));
   p->nx = 100;
@@ -144,6 +145,7 @@ void seb_params_default(seb_params* p) {
 }
 
 const char* seb_status_string(int s) {
+  SEB_RANGE();
   switch (s) {
     case SEB_OK: return "ok";
     case SEB_ERR_INVALID_ARG: return "invalid argument";
@@ -159,11 +161,13 @@ const char* seb_status_string(int s) {
 const char* seb_last_error(const seb_map* m) { return m ? m->err : g_err; }
 
 size_t seb_workspace_bytes(const seb_params* p) {
+  SEB_RANGE();
   if (!p || validate_params(*p) != SEB_OK) return 0;
   return kControlBytes + align256(out_bytes(*p)) + align256(flags_bytes(*p));
 }
 
 int seb_map_create(const seb_params* p, void* ws, size_t bytes, seb_stream_t stream, seb_map** out) {
+  SEB_RANGE();
   if (!p || !out) return fail(nullptr, SEB_ERR_INVALID_ARG, "params or out pointer is NULL");
   *out = nullptr;
   int rc = validate_params(*p);
@@ -195,12 +199,14 @@ int seb_map_create(const seb_params* p, void* ws, size_t bytes, seb_stream_t str
 }
 
 int seb_map_destroy(seb_map* m) {
+  SEB_RANGE();
   if (!m) return SEB_ERR_INVALID_ARG;
   delete m;
   return SEB_OK;
 }
 
 int seb_map_set_stream(seb_map* m, seb_stream_t s) {
+  SEB_RANGE();
   if (!m) return fail(nullptr, SEB_ERR_INVALID_ARG, "map is NULL");
   m->stream = (cudaStream_t)s;
   return SEB_OK;
@@ -227,9 +233,13 @@ static int update_impl(seb_map* m, const void* elev, int64_t oi, int64_t oj, int
   return SEB_OK;
 }
 
-int seb_map_update(seb_map* m, const void* elev, int64_t oi, int64_t oj) { return update_impl(m, elev, oi, oj, 0); }
+int seb_map_update(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
+  SEB_RANGE();
+  return update_impl(m, elev, oi, oj, 0);
+}
 
 static int shift_impl(seb_map* m, const void* elev, int64_t oi, int64_t oj, int early) {
+  SEB_RANGE();
   if (!m) return fail(nullptr, SEB_ERR_INVALID_ARG, "map is NULL");
   if (!m->valid) return update_impl(m, elev, oi, oj, early);
   int rc = check_elev(m, elev);
@@ -290,9 +300,13 @@ static int shift_impl(seb_map* m, const void* elev, int64_t oi, int64_t oj, int 
   return SEB_OK;
 }
 
-int seb_map_shift(seb_map* m, const void* elev, int64_t oi, int64_t oj) { return shift_impl(m, elev, oi, oj, 0); }
+int seb_map_shift(seb_map* m, const void* elev, int64_t oi, int64_t oj) {
+  SEB_RANGE();
+  return shift_impl(m, elev, oi, oj, 0);
+}
 
 int seb_map_shift_batch(seb_map* m, const void* const* elev, const int64_t* origins, int32_t n) {
+  SEB_RANGE();
   if (!m) return fail(nullptr, SEB_ERR_INVALID_ARG, "map is NULL");
   if (n < 0 || (n > 0 && (!elev || !origins)))
     return fail(m, SEB_ERR_INVALID_ARG, "shift batch: NULL window or origin array, or negative count");
@@ -309,6 +323,7 @@ int seb_map_shift_batch(seb_map* m, const void* const* elev, const int64_t* orig
 }
 
 int seb_map_grid(const seb_map* m, int32_t channel, seb_grid* g) {
+  SEB_RANGE();
   if (!m || !g) return fail(nullptr, SEB_ERR_INVALID_ARG, "map or grid is NULL");
   if (channel < 0 || channel >= SEB_N_CH) return fail(nullptr, SEB_ERR_INVALID_ARG, "channel out of range");
   if (!m->valid) return fail(nullptr, SEB_ERR_INVALID_ARG, "map has no outputs before its first update");
@@ -326,6 +341,7 @@ int seb_map_grid(const seb_map* m, int32_t channel, seb_grid* g) {
 }
 
 int seb_map_view(const seb_map* m, seb_view* v) {
+  SEB_RANGE();
   if (!m || !v) return fail(nullptr, SEB_ERR_INVALID_ARG, "map or view is NULL");
   v->out = m->out;
   v->flags = m->flags;
@@ -340,6 +356,7 @@ int seb_map_view(const seb_map* m, seb_view* v) {
 }
 
 int seb_map_copy_out(const seb_map* m, float* out_dev, uint8_t* flags_dev) {
+  SEB_RANGE();
   if (!m) return fail(nullptr, SEB_ERR_INVALID_ARG, "map is NULL");
   if (!out_dev && !flags_dev) return SEB_OK;
   Launch L = base_launch(m, nullptr);
@@ -349,6 +366,7 @@ int seb_map_copy_out(const seb_map* m, float* out_dev, uint8_t* flags_dev) {
 }
 
 int seb_map_check(seb_map* m, int32_t timeout_ms, int64_t* n_fp64, int64_t* n_degenerate) {
+  SEB_RANGE();
   if (!m) return fail(nullptr, SEB_ERR_INVALID_ARG, "map is NULL");
   const auto t0 = std::chrono::steady_clock::now();
   for (;;) {

@@ -337,6 +337,7 @@ int fail(int code, const char* msg) {
 extern "C" {
 
 void seb_elev_params_default(seb_elev_params* p) {
+  SEB_RANGE();
   if (!p) return;
   memset(p, 0, sizeof(*p));
   p->nx = p->ny = 400;
@@ -348,12 +349,14 @@ void seb_elev_params_default(seb_elev_params* p) {
 }
 
 size_t seb_elev_workspace_bytes(const seb_elev_params* p, int64_t max_points) {
+  SEB_RANGE();
   if (!params_ok(p) || max_points < 0) return 0;
   return layout(*p, max_points).total;
 }
 
 int seb_elev_create(const seb_elev_params* p, int64_t max_points, void* ws, size_t bytes, seb_stream_t stream,
                     seb_elev** out) {
+  SEB_RANGE();
   if (!out) return fail(SEB_ERR_INVALID_ARG, "seb_elev_create: out is NULL");
   *out = nullptr;
   if (!params_ok(p) || max_points < 0) return fail(SEB_ERR_INVALID_ARG, "seb_elev_create: bad parameters");
@@ -396,11 +399,13 @@ int seb_elev_create(const seb_elev_params* p, int64_t max_points, void* ws, size
 }
 
 int seb_elev_destroy(seb_elev* e) {
+  SEB_RANGE();
   delete e;
   return SEB_OK;
 }
 
 int seb_elev_set_stream(seb_elev* e, seb_stream_t s) {
+  SEB_RANGE();
   if (!e) return fail(SEB_ERR_INVALID_ARG, "seb_elev_set_stream: NULL");
   e->stream = (cudaStream_t)s;
   return SEB_OK;
@@ -436,6 +441,7 @@ static ElevArgs args_of(const seb_elev* e, const seb_scan_pose* q) {
 }
 
 int seb_elev_integrate(seb_elev* e, const seb_scan_pose* pose, const float* pts, int64_t n) {
+  SEB_RANGE();
   if (!e || !pose) return fail(SEB_ERR_INVALID_ARG, "seb_elev_integrate: NULL map or pose");
   if (n < 0 || n > e->max_points || (n > 0 && !pts))
     return fail(SEB_ERR_INVALID_ARG, "seb_elev_integrate: point count outside [0, max_points] or NULL points");
@@ -482,6 +488,7 @@ int seb_elev_integrate(seb_elev* e, const seb_scan_pose* pose, const float* pts,
 }
 
 int seb_elev_view_get(const seb_elev* e, seb_elev_view* v) {
+  SEB_RANGE();
   if (!e || !v) return fail(SEB_ERR_INVALID_ARG, "seb_elev_view_get: NULL");
   v->height = e->h;
   v->variance = e->s2;
@@ -493,6 +500,7 @@ int seb_elev_view_get(const seb_elev* e, seb_elev_view* v) {
 }
 
 int seb_elev_copy_out(const seb_elev* e, float* height, float* variance) {
+  SEB_RANGE();
   if (!e) return fail(SEB_ERR_INVALID_ARG, "seb_elev_copy_out: NULL");
   ElevArgs A = args_of(e, nullptr);
   const cudaError_t lerr = seb::launch_pdl(copy_out_kernel, dim3(blocks_for((int64_t)e->p.nx * e->p.ny)), dim3(256), 0,

@@ -129,12 +129,14 @@ __global__ void __launch_bounds__(kRowThreads) nn_rows_kernel(const float* __res
 }  // namespace
 
 extern "C" size_t seb_inpaint_workspace_bytes(int32_t nx, int32_t ny) {
+  SEB_RANGE();
   if (nx < 1 || ny < 1 || nx > kMaxSide || ny > kMaxSide) return 0;
   return (size_t)nx * ny * sizeof(int32_t);
 }
 
 extern "C" int seb_inpaint_nearest(const float* elev, int32_t nx, int32_t ny, int32_t max_cells, void* work,
                                    size_t work_bytes, float* out, int32_t* src, seb_stream_t stream) {
+  SEB_RANGE();
   if (!elev || !out || !work) {
     seb::set_error("seb_inpaint_nearest: NULL elevation, output or workspace");
     return SEB_ERR_INVALID_ARG;

@@ -2,11 +2,22 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "seb.h"
 
 namespace seb {
+
+// NVTX range around one entry point (header-only NVTX 3: a no-op unless a profiler such as
+// ncu --nvtx attaches), named after the C function.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define SEB_RANGE() ::seb::NvtxRange seb_nvtx_range_(__func__)
 
 // Thread layout of a CTA: 256 threads, each owning kG = 4 adjacent cells of one row, with
 // 2^log_tpr threads per row.  log_tpr = 3: 32 x 32 cells (interior); 1: 8 x 128 (narrow
@@ -111,11 +122,19 @@ struct QLaunch {
   float gap_fp64;
 };
 
-// Host helpers (seb_tables.cpp).
+// Host helpers (seb_tables.cpp).  build_tables and build_lattice use no heap memory.
 int build_tables(const seb_params& p, Tables* T, int32_t* total_runs);
+// The yaw-0 lattice of the continuous-pose query: the offsets of yaw pair 0 in row-run order.
+int build_lattice(const Tables& T, QTab* Q);
 int validate_params(const seb_params& p);
 size_t out_bytes(const seb_params& p);
 size_t flags_bytes(const seb_params& p);
+
+// Continuous-pose query (seb_query.cu): the lattice and the launch record of a parameter set
+// (validated like seb_query_poses, heap-free), and the launcher.
+int query_setup(const seb_params& p, const void* elev, int64_t origin_i, int64_t origin_j, const float* poses,
+                int64_t n, QTab* Q, QLaunch* L);
+cudaError_t launch_query(const QTab& Q, const QLaunch& L, int elev_dtype, bool backward, cudaStream_t st);
 
 // Kernel launchers (seb_assess.cu).
 cudaError_t launch_assess(const Tables& T, const Launch& L, int elev_dtype, int precision,

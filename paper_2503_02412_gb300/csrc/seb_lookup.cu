@@ -240,6 +240,7 @@ int blocks_for(int64_t n) {
 
 extern "C" int seb_se2_lookup(const seb_grid* g, const float* poses, int64_t n, float fill, float* val, float* grad,
                               uint8_t* flags, seb_stream_t stream) {
+  SEB_RANGE();
   int rc = check_grid(g, "seb_se2_lookup");
   if (rc) return rc;
   if (n < 0 || (n > 0 && (!poses || !val))) {
@@ -258,6 +259,7 @@ extern "C" int seb_se2_lookup(const seb_grid* g, const float* poses, int64_t n, 
 
 extern "C" int seb_se2_lookup_vjp(const seb_grid* g, const float* poses, int64_t n, const float* gval, float* gpose,
                                   seb_stream_t stream) {
+  SEB_RANGE();
   int rc = check_grid(g, "seb_se2_lookup_vjp");
   if (rc) return rc;
   if (n < 0 || (n > 0 && (!poses || !gval || !gpose))) {

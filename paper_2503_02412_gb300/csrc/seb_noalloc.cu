@@ -11,17 +11,15 @@
 //     ordering between them) race on it.  Calls on one stream are safe;
 //   - nothing in it must start at zero: the forward writes the record of every pose the
 //     backward then reads, within the same call;
-//   - the first call on a device resolves the array's device address (cudaGetSymbolAddress
-//     with that device current) and caches it; make that first call before any stream capture.
-#include <math.h>
+//   - the first call on a device (with n >= 1) resolves the array's device address
+//     (cudaGetSymbolAddress with that device current) and caches it.  With lazy module loading
+//     that lookup also loads the module and its 4 MiB array onto the device, so it may fail for
+//     lack of device memory: make that first call once at start-up, before any stream capture
+//     and before the memory budget is taken.
 #include <mutex>
 #include <string.h>
 
 #include "seb_internal.h"
-
-namespace seb {
-cudaError_t launch_query(const QTab& Q, const QLaunch& L, int elev_dtype, bool backward, cudaStream_t st);
-}
 
 namespace {
 
@@ -61,37 +59,12 @@ int scratch_address(float** out) {
   return SEB_OK;
 }
 
-// The yaw-0 footprint lattice, enumerated without heap memory: at yaw 0 the body frame is
-// the grid frame, so (u, v) = (di, dj) in the membership rule; rows ascending, columns
-// ascending (the row-run order of the tables).
-int lattice(const seb_params& p, seb::QTab* Q) {
-  const double a = (double)p.length / (2.0 * (double)p.res);
-  const double b = (double)p.width / (2.0 * (double)p.res);
-  const int B = (int)ceil(sqrt(a * a + b * b)) + 1;
-  int n = 0;
-  for (int dj = -B; dj <= B; ++dj)
-    for (int di = -B; di <= B; ++di) {
-      const bool in = p.shape == SEB_RECT ? (fabs((double)di) <= a + 1e-6 && fabs((double)dj) <= b + 1e-6)
-                                          : ((di / a) * (di / a) + (dj / b) * (dj / b) <= 1.0 + 1e-6);
-      if (!in) continue;
-      if (n >= seb::kMaxLattice || di < -127 || di > 127 || dj < -127 || dj > 127) {
-        seb::set_error("footprint lattice exceeds %d points", seb::kMaxLattice);
-        return SEB_ERR_BAD_SHAPE;
-      }
-      Q->di[n] = (int8_t)di;
-      Q->dj[n] = (int8_t)dj;
-      ++n;
-    }
-  Q->n = n;
-  Q->n_min = p.n_min > 0 ? p.n_min : ((n + 1) / 2 > 3 ? (n + 1) / 2 : 3);
-  return SEB_OK;
-}
-
 }  // namespace
 
 extern "C" int seb_query_poses_grad_noalloc(const seb_params* p, const void* elev, int64_t oi, int64_t oj,
                                             const float* poses, int64_t n, const float* grad_out, float* out,
                                             uint8_t* flags, float* grad_pose, seb_stream_t stream) {
+  SEB_RANGE();
   if (!p || !elev || n < 0 || (n > 0 && (!poses || !grad_out || !out || !flags || !grad_pose))) {
     seb::set_error("seb_query_poses_grad_noalloc: NULL pointer or negative count");
     return SEB_ERR_INVALID_ARG;
@@ -102,32 +75,15 @@ extern "C" int seb_query_poses_grad_noalloc(const seb_params* p, const void* ele
                    (long long)n, (long long)kNoAllocMaxPoses);
     return SEB_ERR_INVALID_ARG;
   }
-  int rc = seb::validate_params(*p);
-  if (rc) return rc;
+  // the same lattice, validation and launch record as seb_query_poses (no heap memory)
   seb::QTab Q;
-  rc = lattice(*p, &Q);
+  seb::QLaunch L;
+  int rc = seb::query_setup(*p, elev, oi, oj, poses, n, &Q, &L);
   if (rc) return rc;
   if (n == 0) return SEB_OK;
   float* saved = nullptr;
   rc = scratch_address(&saved);
   if (rc) return rc;
-  seb::QLaunch L;
-  memset(&L, 0, sizeof(L));
-  L.elev = elev;
-  L.nx = p->nx;
-  L.ny = p->ny;
-  L.res = p->res;
-  L.oi = (double)oi;
-  L.oj = (double)oj;
-  L.poses = poses;
-  L.n = n;
-  L.kappa_max = p->kappa_max;
-  L.phi_x_max = p->phi_x_max;
-  L.phi_y_max = p->phi_y_max;
-  L.w0 = p->w[0];
-  L.w1 = p->w[1];
-  L.w2 = p->w[2];
-  L.gap_fp64 = p->gap_fp64;
   L.out = out;
   L.flags = flags;
   L.saved = saved;

@@ -593,38 +593,6 @@ cudaError_t launch_q(const QTab& Q, const QLaunch& L, bool backward, cudaStream_
 
 }  // namespace
 
-int build_query_table(const seb_params& p, QTab* Q) {
-  Tables* T = new Tables;
-  int rc = build_tables(p, T, nullptr);
-  if (rc) {
-    delete T;
-    return rc;
-  }
-  int n = 0;
-  for (int r = T->run_start[0]; r < T->run_start[1]; ++r) {
-    const uint32_t pk = T->runs[r];
-    const int y = (int)(pk & 0xff) - 128, lo = (int)((pk >> 8) & 0xff) - 128, hi = (int)((pk >> 16) & 0xff) - 128;
-    for (int x = lo; x <= hi; ++x) {
-      if (n >= kMaxLattice) {
-        delete T;
-        set_error("footprint lattice exceeds %d points", kMaxLattice);
-        return SEB_ERR_BAD_SHAPE;
-      }
-      Q->di[n] = (int8_t)x;
-      Q->dj[n] = (int8_t)y;
-      ++n;
-    }
-  }
-  Q->n = n;
-  Q->n_min = T->n_min[0];
-  delete T;
-  if (n > 32 * kPPL) {
-    set_error("footprint lattice exceeds %d points", 32 * kPPL);
-    return SEB_ERR_BAD_SHAPE;
-  }
-  return SEB_OK;
-}
-
 cudaError_t launch_query(const QTab& Q, const QLaunch& L, int elev_dtype, bool backward, cudaStream_t st) {
   switch (elev_dtype) {
     case SEB_F32: return launch_q<float>(Q, L, backward, st);
@@ -633,53 +601,58 @@ cudaError_t launch_query(const QTab& Q, const QLaunch& L, int elev_dtype, bool b
   }
 }
 
+int query_setup(const seb_params& p, const void* elev, int64_t oi, int64_t oj, const float* poses, int64_t n,
+                QTab* Q, QLaunch* L) {
+  int rc = validate_params(p);
+  if (rc) return rc;
+  Tables T;  // on the stack: the allocation-free query shares this path
+  rc = build_tables(p, &T, nullptr);
+  if (rc) return rc;
+  rc = build_lattice(T, Q);
+  if (rc) return rc;
+  if (Q->n > 32 * kPPL) {
+    set_error("footprint lattice exceeds %d points", 32 * kPPL);
+    return SEB_ERR_BAD_SHAPE;
+  }
+  memset(L, 0, sizeof(*L));
+  L->elev = elev;
+  L->nx = p.nx;
+  L->ny = p.ny;
+  L->res = p.res;
+  L->oi = (double)oi;
+  L->oj = (double)oj;
+  L->poses = poses;
+  L->n = n;
+  L->kappa_max = p.kappa_max;
+  L->phi_x_max = p.phi_x_max;
+  L->phi_y_max = p.phi_y_max;
+  L->w0 = p.w[0];
+  L->w1 = p.w[1];
+  L->w2 = p.w[2];
+  L->gap_fp64 = p.gap_fp64;
+  return SEB_OK;
+}
+
 }  // namespace seb
 
 using namespace seb;
 
-static QLaunch query_launch(const seb_params* p, const void* elev, int64_t oi, int64_t oj, const float* poses,
-                            int64_t n) {
-  QLaunch L;
-  memset(&L, 0, sizeof(L));
-  L.elev = elev;
-  L.nx = p->nx;
-  L.ny = p->ny;
-  L.res = p->res;
-  L.oi = (double)oi;
-  L.oj = (double)oj;
-  L.poses = poses;
-  L.n = n;
-  L.kappa_max = p->kappa_max;
-  L.phi_x_max = p->phi_x_max;
-  L.phi_y_max = p->phi_y_max;
-  L.w0 = p->w[0];
-  L.w1 = p->w[1];
-  L.w2 = p->w[2];
-  L.gap_fp64 = p->gap_fp64;
-  return L;
-}
-
 extern "C" int seb_query_poses(const seb_params* p, const void* elev, int64_t oi, int64_t oj,
                                const float* poses, int64_t n, float* out, uint8_t* flags, float* saved,
                                seb_stream_t stream) {
+  SEB_RANGE();
   if (!p || !elev || (n > 0 && (!poses || !out || !flags)) || n < 0) {
     set_error("seb_query_poses: NULL pointer or negative count");
     return SEB_ERR_INVALID_ARG;
   }
-  int rc = validate_params(*p);
+  QTab Q;
+  QLaunch L;
+  const int rc = query_setup(*p, elev, oi, oj, poses, n, &Q, &L);
   if (rc) return rc;
-  QTab* Q = new QTab;
-  rc = build_query_table(*p, Q);
-  if (rc) {
-    delete Q;
-    return rc;
-  }
-  QLaunch L = query_launch(p, elev, oi, oj, poses, n);
   L.out = out;
   L.flags = flags;
   L.saved = saved;
-  cudaError_t e = launch_query(*Q, L, p->elev_dtype, false, (cudaStream_t)stream);
-  delete Q;
+  cudaError_t e = launch_query(Q, L, p->elev_dtype, false, (cudaStream_t)stream);
   if (e != cudaSuccess) {
     set_error("seb_query_poses launch: %s", cudaGetErrorString(e));
     return SEB_ERR_CUDA;
@@ -690,24 +663,19 @@ extern "C" int seb_query_poses(const seb_params* p, const void* elev, int64_t oi
 extern "C" int seb_query_poses_backward(const seb_params* p, const void* elev, int64_t oi, int64_t oj,
                                         const float* poses, const float* saved, const float* gout, float* gpose,
                                         int64_t n, seb_stream_t stream) {
+  SEB_RANGE();
   if (!p || !elev || (n > 0 && (!poses || !gout || !gpose)) || n < 0) {
     set_error("seb_query_poses_backward: NULL pointer or negative count");
     return SEB_ERR_INVALID_ARG;
   }
-  int rc = validate_params(*p);
+  QTab Q;
+  QLaunch L;
+  const int rc = query_setup(*p, elev, oi, oj, poses, n, &Q, &L);
   if (rc) return rc;
-  QTab* Q = new QTab;
-  rc = build_query_table(*p, Q);
-  if (rc) {
-    delete Q;
-    return rc;
-  }
-  QLaunch L = query_launch(p, elev, oi, oj, poses, n);
   L.saved = const_cast<float*>(saved);
   L.gout = gout;
   L.gpose = gpose;
-  cudaError_t e = launch_query(*Q, L, p->elev_dtype, true, (cudaStream_t)stream);
-  delete Q;
+  cudaError_t e = launch_query(Q, L, p->elev_dtype, true, (cudaStream_t)stream);
   if (e != cudaSuccess) {
     set_error("seb_query_poses_backward launch: %s", cudaGetErrorString(e));
     return SEB_ERR_CUDA;

@@ -281,12 +281,14 @@ __global__ void __launch_bounds__(kRowThreads) rows16_kernel(const SdfArgs A, in
 }  // namespace
 
 extern "C" size_t seb_sdf_workspace_bytes(int32_t nx, int32_t ny, int32_t n_yaw) {
+  SEB_RANGE();
   if (nx < 1 || ny < 1 || n_yaw < 1 || nx > kMaxSide || ny > kMaxSide) return 0;
   return (size_t)nx * ny * n_yaw * sizeof(uint32_t);
 }
 
 extern "C" int seb_risk_sdf(const seb_grid* g, float risk_obstacle, float clamp, void* work, size_t work_bytes,
                             float* sdf, seb_stream_t stream) {
+  SEB_RANGE();
   if (!g || !g->data || !sdf || !work) {
     seb::set_error("seb_risk_sdf: NULL grid, output or workspace");
     return SEB_ERR_INVALID_ARG;

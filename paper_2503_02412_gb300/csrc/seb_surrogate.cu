@@ -831,6 +831,7 @@ struct seb_sur {
   seb_sur_view v;
   uint32_t* err;
   int32_t engine;  // SEB_SUR_SIMT | SEB_SUR_TCGEN05 for the 32 -> 32 layers
+  int64_t step;    // Adam step of the last seb_sur_train_step (0 after init)
 };
 
 namespace {
@@ -909,11 +910,13 @@ T* at(const seb_sur* h, size_t off) {
 extern "C" {
 
 size_t seb_sur_workspace_bytes(const seb_params* p, int32_t max_batch) {
+  SEB_RANGE();
   if (!p || seb::validate_params(*p) != SEB_OK || max_batch < 1) return 0;
   return sizes(*p, 2 * p->n_yaw, max_batch).total;
 }
 
 int seb_sur_create(const seb_params* p, int32_t max_batch, void* ws, size_t bytes, seb_stream_t stream, seb_sur** out) {
+  SEB_RANGE();
   if (!p || !out || max_batch < 1) return fail("seb_sur_create: NULL argument or batch < 1");
   *out = nullptr;
   int rc = seb::validate_params(*p);
@@ -986,31 +989,37 @@ int seb_sur_create(const seb_params* p, int32_t max_batch, void* ws, size_t byte
 }
 
 int seb_sur_destroy(seb_sur* h) {
+  SEB_RANGE();
   if (!h) return SEB_ERR_INVALID_ARG;
   delete h;
   return SEB_OK;
 }
 
 int seb_sur_set_stream(seb_sur* h, seb_stream_t s) {
+  SEB_RANGE();
   if (!h) return fail("surrogate handle is NULL");
   h->stream = (cudaStream_t)s;
   return SEB_OK;
 }
 
 int seb_sur_set_engine(seb_sur* h, int32_t engine) {
+  SEB_RANGE();
   if (!h || (engine != SEB_SUR_SIMT && engine != SEB_SUR_TCGEN05)) return fail("seb_sur_set_engine: bad engine");
   h->engine = engine;
   return SEB_OK;
 }
 
 int seb_sur_view_get(const seb_sur* h, seb_sur_view* v) {
+  SEB_RANGE();
   if (!h || !v) return fail("surrogate handle or view is NULL");
   *v = h->v;
   return SEB_OK;
 }
 
 int seb_sur_init(seb_sur* h, uint64_t seed) {
+  SEB_RANGE();
   if (!h) return fail("surrogate handle is NULL");
+  h->step = 0;
   init_kernel<<<grid_for(h->PL.n, 256), 256, 0, h->stream>>>(at<float>(h, h->v.master), at<float>(h, h->v.adam_m),
                                                              at<float>(h, h->v.adam_v), at<bf16>(h, h->v.weights_bf16),
                                                              h->PL, seed);
@@ -1019,6 +1028,7 @@ int seb_sur_init(seb_sur* h, uint64_t seed) {
 
 int seb_terrain_bumpy(const float* params_dev, int32_t n, int32_t nx, int32_t ny, float res, uint64_t seed,
                       float* out_dev, seb_stream_t stream) {
+  SEB_RANGE();
   if (!params_dev || !out_dev || n < 0 || nx < 1 || ny < 1 || !(res > 0.f)) return fail("seb_terrain_bumpy: bad args");
   if (n == 0) return SEB_OK;
   terrain_kernel<<<grid_for((int64_t)n * nx * ny, 256), 256, 0, (cudaStream_t)stream>>>(params_dev, n, nx, ny, res,
@@ -1028,6 +1038,7 @@ int seb_terrain_bumpy(const float* params_dev, int32_t n, int32_t nx, int32_t ny
 
 int seb_sur_gather(seb_sur* h, const float* elev, const float* exact, int32_t nx, int32_t ny, const int32_t* centres,
                    int32_t n, int32_t offset) {
+  SEB_RANGE();
   if (!h || !elev || !exact || !centres || n < 0 || offset < 0 || offset + n > h->max_batch)
     return fail("seb_sur_gather: bad args (offset + n must be <= max_batch)");
   if (n == 0) return SEB_OK;
@@ -1073,14 +1084,17 @@ static int forward_batch(seb_sur* h, int B) {
 }
 
 int seb_sur_forward(seb_sur* h, int32_t batch) {
+  SEB_RANGE();
   if (!h || batch < 1 || batch > h->max_batch) return fail("seb_sur_forward: batch out of range");
   return forward_batch(h, batch);
 }
 
 int seb_sur_train_step(seb_sur* h, int32_t B, float lr, int32_t step, float* loss_dev) {
+  SEB_RANGE();
   if (!h || B < 1 || B > h->max_batch || step < 1) return fail("seb_sur_train_step: bad batch or step");
   int rc = forward_batch(h, B);
   if (rc) return rc;
+  h->step = step;
   cudaStream_t st = h->stream;
   const int nout = h->nout;
   const int64_t P = (int64_t)B * kOutSide * kOutSide;
@@ -1134,8 +1148,84 @@ int seb_sur_train_step(seb_sur* h, int32_t B, float lr, int32_t step, float* los
   return cuda_check(cudaGetLastError(), "surrogate train step");
 }
 
+// Checkpoint image: a 64-byte header, then the FP32 master weights, the Adam first and second
+// moments and the BF16 weights, each [n_params].
+struct CkptHeader {
+  char magic[8];      // "SEBSUR01"
+  int64_t n_params;
+  int32_t n_out, n_yaw;
+  int64_t step;
+  uint64_t bytes;     // whole image
+  int32_t engine, pad;
+  int64_t reserved[2];
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
+
+static size_t ckpt_bytes(const seb_sur* h) { return sizeof(CkptHeader) + (size_t)h->PL.n * (3 * 4 + 2); }
+
+size_t seb_sur_state_bytes(const seb_sur* h) { return h ? ckpt_bytes(h) : 0; }
+
+int seb_sur_save(seb_sur* h, void* dst, size_t bytes) {
+  SEB_RANGE();
+  if (!h || !dst) return fail("seb_sur_save: NULL handle or buffer");
+  if (bytes < ckpt_bytes(h)) return fail("seb_sur_save: buffer of %zu bytes < %zu", bytes, ckpt_bytes(h));
+  CkptHeader hd;
+  memset(&hd, 0, sizeof(hd));
+  memcpy(hd.magic, "SEBSUR01", 8);
+  hd.n_params = h->PL.n;
+  hd.n_out = h->nout;
+  hd.n_yaw = h->p.n_yaw;
+  hd.step = h->step;
+  hd.bytes = ckpt_bytes(h);
+  hd.engine = h->engine;
+  uint8_t* o = static_cast<uint8_t*>(dst);
+  memcpy(o, &hd, sizeof(hd));
+  o += sizeof(hd);
+  const size_t n4 = (size_t)h->PL.n * 4, n2 = (size_t)h->PL.n * 2;
+  const size_t src[3] = {h->v.master, h->v.adam_m, h->v.adam_v};
+  for (int i = 0; i < 3; ++i, o += n4) {
+    int rc = cuda_check(cudaMemcpyAsync(o, h->ws + src[i], n4, cudaMemcpyDeviceToHost, h->stream), "seb_sur_save");
+    if (rc) return rc;
+  }
+  int rc = cuda_check(cudaMemcpyAsync(o, h->ws + h->v.weights_bf16, n2, cudaMemcpyDeviceToHost, h->stream),
+                      "seb_sur_save");
+  if (rc) return rc;
+  return cuda_check(cudaStreamSynchronize(h->stream), "seb_sur_save (synchronise)");
+}
+
+int seb_sur_load(seb_sur* h, const void* src, size_t bytes) {
+  SEB_RANGE();
+  if (!h || !src) return fail("seb_sur_load: NULL handle or buffer");
+  CkptHeader hd;
+  if (bytes < sizeof(hd)) return fail("seb_sur_load: image of %zu bytes has no header", bytes);
+  memcpy(&hd, src, sizeof(hd));
+  if (memcmp(hd.magic, "SEBSUR01", 8) != 0) return fail("seb_sur_load: not a surrogate checkpoint");
+  if (hd.n_params != h->PL.n || hd.n_out != h->nout || hd.n_yaw != h->p.n_yaw)
+    return fail("seb_sur_load: checkpoint of %lld parameters / %d outputs / %d yaw bins does not fit this network "
+                "(%lld / %d / %d)", (long long)hd.n_params, hd.n_out, hd.n_yaw, (long long)h->PL.n, h->nout,
+                h->p.n_yaw);
+  if (hd.bytes != ckpt_bytes(h) || bytes < hd.bytes) return fail("seb_sur_load: truncated checkpoint");
+  const uint8_t* i = static_cast<const uint8_t*>(src) + sizeof(hd);
+  const size_t n4 = (size_t)h->PL.n * 4, n2 = (size_t)h->PL.n * 2;
+  const size_t dst[3] = {h->v.master, h->v.adam_m, h->v.adam_v};
+  for (int k = 0; k < 3; ++k, i += n4) {
+    int rc = cuda_check(cudaMemcpyAsync(h->ws + dst[k], i, n4, cudaMemcpyHostToDevice, h->stream), "seb_sur_load");
+    if (rc) return rc;
+  }
+  int rc = cuda_check(cudaMemcpyAsync(h->ws + h->v.weights_bf16, i, n2, cudaMemcpyHostToDevice, h->stream),
+                      "seb_sur_load");
+  if (rc) return rc;
+  rc = cuda_check(cudaStreamSynchronize(h->stream), "seb_sur_load (synchronise)");
+  if (rc) return rc;
+  h->step = hd.step;
+  return SEB_OK;
+}
+
+int64_t seb_sur_step(const seb_sur* h) { return h ? h->step : -1; }
+
 int seb_sur_infer(seb_sur* h, const float* elev, float step, int32_t radius, int32_t exact_fallback, float* out,
                   uint8_t* flags, uint8_t* mask_out) {
+  SEB_RANGE();
   if (!h || !elev || !out || !flags || radius < 0) return fail("seb_sur_infer: bad args");
   cudaStream_t st = h->stream;
   const int nx = h->p.nx, ny = h->p.ny;

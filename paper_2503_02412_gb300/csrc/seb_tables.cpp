@@ -13,8 +13,6 @@
 #include <stdio.h>
 #include <string.h>
 
-#include <vector>
-
 #include "seb_internal.h"
 
 namespace seb {
@@ -48,58 +46,67 @@ static bool member(const seb_params& p, double c, double s, int di, int dj) {
   return (u / a) * (u / a) + (v / b) * (v / b) <= 1.0 + 1e-6;
 }
 
-// Offsets of yaw pair q in row-run order.
-static void enumerate(const seb_params& p, int q, std::vector<int>& di, std::vector<int>& dj) {
+// Offsets of yaw pair q in row-run order (dj ascending, then di ascending), handed to visit(di, dj)
+// one at a time: no heap memory, so every caller (the allocation-free query included) enumerates
+// the same sets with the same rule.
+template <typename Visit>
+static void enumerate(const seb_params& p, int q, Visit visit) {
   const double a = (double)p.length / (2.0 * (double)p.res);
   const double b = (double)p.width / (2.0 * (double)p.res);
   const int B = (int)ceil(sqrt(a * a + b * b)) + 1;
   const double th = 2.0 * M_PI * (double)q / (double)p.n_yaw;
   const double c = cos(th), s = sin(th);
-  di.clear();
-  dj.clear();
   for (int y = -B; y <= B; ++y)
     for (int x = -B; x <= B; ++x)
-      if (member(p, c, s, x, y)) {
-        di.push_back(x);
-        dj.push_back(y);
-      }
+      if (member(p, c, s, x, y)) visit(x, y);
 }
 
 int build_tables(const seb_params& p, Tables* T, int32_t* total_runs) {
   memset(T, 0, sizeof(*T));
   const int half = p.n_yaw / 2;
   T->n_pairs = half;
-  std::vector<int> di, dj;
   int nr = 0, rx = 0, ry = 0;
   for (int q = 0; q < half; ++q) {
-    enumerate(p, q, di, dj);
-    const int n = (int)di.size();
     T->run_start[q] = nr;
-    int64_t m[6] = {n, 0, 0, 0, 0, 0};
-    for (int i = 0; i < n; ++i) {
-      m[1] += di[i];
-      m[2] += dj[i];
-      m[3] += (int64_t)di[i] * di[i];
-      m[4] += (int64_t)di[i] * dj[i];
-      m[5] += (int64_t)dj[i] * dj[i];
-      rx = abs(di[i]) > rx ? abs(di[i]) : rx;
-      ry = abs(dj[i]) > ry ? abs(dj[i]) : ry;
-    }
-    for (int i = 0; i < n;) {  // maximal runs of consecutive di in one row
-      int j = i;
-      while (j + 1 < n && dj[j + 1] == dj[i] && di[j + 1] == di[j] + 1) ++j;
+    int64_t m[6] = {0, 0, 0, 0, 0, 0};
+    // maximal runs of consecutive di in one row, closed when the next offset does not extend them
+    int run_dj = 0, run_lo = 0, run_hi = 0;
+    bool open = false, bad = false;
+    auto close = [&]() {
+      if (!open || bad) return;
       if (nr >= kMaxRuns) {
         set_error("footprint needs more than %d row runs", kMaxRuns);
-        return SEB_ERR_BAD_SHAPE;
+        bad = true;
+        return;
       }
-      if (dj[i] < -127 || dj[i] > 127 || di[i] < -127 || di[j] > 127) {
+      if (run_dj < -127 || run_dj > 127 || run_lo < -127 || run_hi > 127) {
         set_error("footprint reach exceeds 127 cells");
-        return SEB_ERR_BAD_SHAPE;
+        bad = true;
+        return;
       }
-      T->runs[nr++] = (uint32_t)(dj[i] + 128) | ((uint32_t)(di[i] + 128) << 8) |
-                      ((uint32_t)(di[j] + 128) << 16);
-      i = j + 1;
-    }
+      T->runs[nr++] = (uint32_t)(run_dj + 128) | ((uint32_t)(run_lo + 128) << 8) | ((uint32_t)(run_hi + 128) << 16);
+    };
+    enumerate(p, q, [&](int di, int dj) {
+      m[0] += 1;
+      m[1] += di;
+      m[2] += dj;
+      m[3] += (int64_t)di * di;
+      m[4] += (int64_t)di * dj;
+      m[5] += (int64_t)dj * dj;
+      rx = abs(di) > rx ? abs(di) : rx;
+      ry = abs(dj) > ry ? abs(dj) : ry;
+      if (open && dj == run_dj && di == run_hi + 1) {
+        run_hi = di;
+        return;
+      }
+      close();
+      open = true;
+      run_dj = dj;
+      run_lo = run_hi = di;
+    });
+    close();
+    if (bad) return SEB_ERR_BAD_SHAPE;
+    const int n = (int)m[0];
     for (int t = 0; t < 6; ++t) {
       if (m[t] > (1 << 24) || m[t] < -(1 << 24)) {
         set_error("footprint moments exceed 2^24");
@@ -136,10 +143,31 @@ int build_tables(const seb_params& p, Tables* T, int32_t* total_runs) {
   return SEB_OK;
 }
 
+int build_lattice(const Tables& T, QTab* Q) {
+  int n = 0;
+  for (int r = T.run_start[0]; r < T.run_start[1]; ++r) {
+    const uint32_t pk = T.runs[r];
+    const int y = (int)(pk & 0xff) - 128, lo = (int)((pk >> 8) & 0xff) - 128, hi = (int)((pk >> 16) & 0xff) - 128;
+    for (int x = lo; x <= hi; ++x) {
+      if (n >= kMaxLattice) {
+        set_error("footprint lattice exceeds %d points", kMaxLattice);
+        return SEB_ERR_BAD_SHAPE;
+      }
+      Q->di[n] = (int8_t)x;
+      Q->dj[n] = (int8_t)y;
+      ++n;
+    }
+  }
+  Q->n = n;
+  Q->n_min = T.n_min[0];
+  return SEB_OK;
+}
+
 }  // namespace seb
 
 extern "C" int seb_footprint_table(const seb_params* p, int32_t k, int32_t* di, int32_t* dj,
                                    int32_t cap) {
+  SEB_RANGE();
   if (!p) return SEB_ERR_INVALID_ARG;
   int rc = seb::validate_params(*p);
   if (rc) return rc;

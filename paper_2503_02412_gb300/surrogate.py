@@ -133,12 +133,18 @@ class Surrogate:
     def train(self, n_patches, batch=256, lr=2e-3, seed=1000, log_every=0):
         rng = np.random.default_rng(seed)
         steps = (n_patches + batch - 1) // batch
+        return self.train_steps(rng, 0, steps, steps, batch, lr, log_every)
+
+    def train_steps(self, rng, first, count, total, batch=256, lr=2e-3, log_every=0):
+        """Steps first .. first + count - 1 of a run of `total` steps (cosine learning-rate
+        schedule over the run), drawing terrain and patches from `rng`.  A run split into calls,
+        or resumed from a checkpoint with the generator state restored, repeats the same steps."""
         losses = []
-        for i in range(steps):
-            cur_lr = lr * 0.5 * (1 + math.cos(math.pi * i / steps))  # cosine schedule
+        for i in range(first, first + count):
+            cur_lr = lr * 0.5 * (1 + math.cos(math.pi * i / total))  # cosine schedule
             self.make_batch(rng, batch)
             self.train_step(batch, cur_lr)
-            if log_every and (i % log_every == 0 or i == steps - 1):
+            if log_every and (i % log_every == 0 or i == total - 1):
                 losses.append((i, float(self.loss.item())))
         return losses
 
@@ -159,14 +165,14 @@ class Surrogate:
                           fl.data_ptr(), mask.data_ptr())
 
     def state_dict(self):
-        n = self.n_params
-        return {"master": self.master.clone(), "adam_m": self._f32(self.v.adam_m, n).clone(),
-                "adam_v": self._f32(self.v.adam_v, n).clone(), "step": self.step}
+        """Checkpoint through the C ABI (seb_sur_save: master weights, Adam moments, BF16 weights
+        and the Adam step)."""
+        abi.seb_sur_set_stream(self.handle, self._stream())
+        return {"image": abi.seb_sur_save(self.handle), "step": self.step}
 
     def load_state_dict(self, sd):
-        n = self.n_params
-        self.master.copy_(sd["master"])
-        self._f32(self.v.adam_m, n).copy_(sd["adam_m"])
-        self._f32(self.v.adam_v, n).copy_(sd["adam_v"])
-        self.weights_bf16.copy_(sd["master"].to(torch.bfloat16))
-        self.step = int(sd["step"])
+        abi.seb_sur_set_stream(self.handle, self._stream())
+        abi.seb_sur_load(self.handle, sd["image"])
+        self.step = abi.seb_sur_step(self.handle)
+        if self.step != int(sd["step"]):
+            raise ValueError("checkpoint step and image disagree")

@@ -8,41 +8,73 @@ threshold (roughness within 3e-5 of kappa_max, |pitch| / |roll| within 1e-4 of p
 phi_y_max) may legitimately take the other branch in FP32; they are counted, not failed.
 Cells flagged DEGENERATE by either side are excluded from the value checks (their outputs
 are NaN by definition); the UNKNOWN bit is an integer decision and must match exactly.
-Cells whose oracle relative eigen-gap (lambda_mid - lambda_min) / trace is below GAP_MIN are
-ill-conditioned: their normal moves by dCov / gap, and FP32 moment sums (|dCov| ~ 1e-9 m^2
-on these maps) cannot fix it to 1e-4 rad; they are counted and excluded from value checks.
+
+Ill-conditioned cells (oracle relative eigen-gap g = (lambda_mid - lambda_min) / trace below
+GAP_MIN) are checked against a bound that grows as the gap shrinks, not skipped.  The kernel's
+moment sums are FP32, so its covariance carries an error ||dC|| <= C_GAP u tr(C) (u = 2^-24,
+the unit roundoff; C_GAP bounds the growth of the rounding error over the ~250 summed points
+and the ratio of the raw second moments about the block's reference height to the trace).
+By the Davis-Kahan sin-theta theorem the normal then moves by at most ||dC|| / (lambda_mid -
+lambda_min) = C_GAP u / g radians, whichever eigen-solve follows (the kernel redoes these solves
+in FP64).  Hence, per ill-conditioned cell:
+  pitch, roll   <= max(1e-4, B),          B = C_GAP u / g
+  z             <= max(1e-4, B R / n_z^2) (the plane height at the centre is the mean height
+                                           plus the slope n_xy / n_z times the footprint mean's
+                                           offset, at most the reach R in metres; the slope moves
+                                           by the normal's angle over n_z^2, n_z from the oracle)
+  roughness     <= 3e-5                   (an eigenvalue moves by ||dC|| only: no gap division)
+  risk          <= max(1e-4, B (w1 / phi_x + w2 / phi_y) + 1e-4)
+and the risk branch may flip where an oracle angle lies within max(1e-4, B) of its limit.  The
+number of such cells and the largest |error| / bound are reported (`ill`, `ill_ratio`).
 """
 import numpy as np
 
 TOL = {0: 1e-4, 1: 1e-4, 2: 1e-4, 3: 3e-5, 4: 1e-4}
 GAP_MIN = 1e-4
+U32 = 2.0 ** -24
+C_GAP = 256.0
 UNKNOWN, OBSTACLE, DEGENERATE, FP64 = 1, 2, 4, 8
 
 
-def near_threshold(ref, kappa_max=0.1, phi_x=0.52, phi_y=0.52, margin=None):
+def ill_bound(gap):
+    """Angle bound (rad) of a cell with relative eigen-gap `gap` (see the module docstring)."""
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return C_GAP * U32 / np.maximum(gap, 1e-300)
+
+
+def near_threshold(ref, kappa_max=0.1, phi_x=0.52, phi_y=0.52, margin=None, angle_margin=None):
     """ref: [..., 5] oracle outputs -> bool mask of cells whose roughness / |pitch| / |roll|
-    lies within its tolerance (or the given margin) of the matching risk threshold."""
+    lies within its tolerance (or the given margin; angle_margin, a scalar or per-cell array,
+    overrides it for the angles) of the matching risk threshold."""
     mk = TOL[3] if margin is None else margin
     ma = TOL[1] if margin is None else margin
+    if angle_margin is not None:
+        ma = angle_margin
     with np.errstate(invalid="ignore"):
         return ((np.abs(ref[..., 3] - kappa_max) < mk) | (np.abs(np.abs(ref[..., 1]) - phi_x) < ma)
                 | (np.abs(np.abs(ref[..., 2]) - phi_y) < ma))
 
 
-def compare(gpu, gflags, ref, rflags, kappa_max=0.1, phi_x=0.52, phi_y=0.52, tol=None, label="", gap=None):
-    """gpu/ref: [n, 5]; flags [n].  Returns a dict of statistics; raises AssertionError on a
-    violation outside the stated exclusions."""
+def compare(gpu, gflags, ref, rflags, kappa_max=0.1, phi_x=0.52, phi_y=0.52, tol=None, label="", gap=None,
+            reach_m=0.6, w=(1 / 3, 1 / 3, 1 / 3)):
+    """gpu/ref: [n, 5]; flags [n]; gap: the oracle's relative eigen-gaps [n] (optional);
+    reach_m: the footprint's largest offset in metres (0.6 covers the 0.9 x 0.6 m and
+    0.6 x 0.4 m footprints).  Returns a dict of statistics; raises AssertionError on a violation
+    outside the stated exclusions."""
     tol = dict(TOL, **(tol or {}))
     gflags = gflags.astype(np.uint8) & 7
     rflags = rflags.astype(np.uint8) & 7
     assert np.array_equal(gflags & UNKNOWN, rflags & UNKNOWN), f"{label}: UNKNOWN bits differ"
     near = near_threshold(ref, kappa_max, phi_x, phi_y)
     degen = ((gflags | rflags) & DEGENERATE) != 0
-    ill = np.zeros_like(degen)
+    n = len(gpu)
+    ill = np.zeros(n, bool)
+    bound = np.zeros(n)
     if gap is not None:
         with np.errstate(invalid="ignore"):
-            ill = (gap < GAP_MIN) & ((rflags & UNKNOWN) == 0)
-        degen = degen | ill
+            ill = (gap < GAP_MIN) & ((rflags & UNKNOWN) == 0) & ~degen
+        bound = np.where(ill, ill_bound(gap), 0.0)
+        near = near | (ill & near_threshold(ref, kappa_max, phi_x, phi_y, angle_margin=np.maximum(bound, tol[1])))
     assessed = ((rflags & UNKNOWN) == 0) & ~degen
     flag_mismatch = (gflags != rflags) & ~near & ~degen
     if flag_mismatch.any():
@@ -50,19 +82,40 @@ def compare(gpu, gflags, ref, rflags, kappa_max=0.1, phi_x=0.52, phi_y=0.52, tol
         raise AssertionError(f"{label}: {flag_mismatch.sum()} flag mismatches away from thresholds; "
                              f"idx {i.tolist()} gpu {gpu[i].tolist()} {gflags[i].tolist()} "
                              f"ref {ref[i].tolist()} {rflags[i].tolist()}")
-    stats = dict(n=len(gpu), assessed=int(assessed.sum()), near=int((near & assessed).sum()),
-                 degenerate=int(degen.sum()), ill=int(ill.sum()))
-    assert stats["ill"] <= max(8, 1e-3 * len(gpu)), f"{label}: {stats['ill']} ill-conditioned cells"
+    stats = dict(n=n, assessed=int(assessed.sum()), near=int((near & assessed).sum()),
+                 degenerate=int(degen.sum()), ill=int(ill.sum()), ill_ratio=0.0)
+    # per-cell tolerance of each channel: the plain tolerance, widened for ill-conditioned cells
+    with np.errstate(invalid="ignore"):
+        sp, sr = np.sin(ref[:, 1]), np.sin(ref[:, 2])
+        nz = np.sqrt(np.clip(1.0 - sp * sp - sr * sr, 1e-12, 1.0))
+    limit = {ch: np.full(n, tol[ch]) for ch in range(5)}
+    limit[1] = np.maximum(tol[1], bound)
+    limit[2] = np.maximum(tol[2], bound)
+    limit[0] = np.maximum(tol[0], np.where(ill, bound * reach_m / (nz * nz), 0.0))
+    limit[4] = np.maximum(tol[4], np.where(ill, bound * (w[1] / phi_x + w[2] / phi_y) + tol[4], 0.0))
     for ch in range(5):
         sel = assessed & ~(near if ch == 4 else np.zeros_like(near))
         d = np.abs(gpu[sel, ch].astype(np.float64) - ref[sel, ch])
-        mx = float(d.max()) if d.size else 0.0
+        lim = limit[ch][sel]
+        plain = ~ill[sel]
+        mx = float(d[plain].max()) if plain.any() else 0.0
         stats[f"max{ch}"] = mx
-        stats[f"p99_{ch}"] = float(np.percentile(d, 99)) if d.size else 0.0
-        assert mx <= tol[ch], f"{label}: channel {ch} max |err| {mx:.3e} > {tol[ch]:.1e}"
-    flips = (np.abs(gpu[:, 4] - ref[:, 4]) > tol[4]) & assessed & near
+        stats[f"p99_{ch}"] = float(np.percentile(d[plain], 99)) if plain.any() else 0.0
+        if (~plain).any():
+            stats[f"ill_max{ch}"] = float(d[~plain].max())
+            stats["ill_ratio"] = max(stats["ill_ratio"], float((d[~plain] / lim[~plain]).max()))
+        bad = ~(d <= lim)
+        if bad.any():
+            i = np.flatnonzero(sel)[np.flatnonzero(bad)[:4]]
+            raise AssertionError(f"{label}: channel {ch}: {int(bad.sum())} cells above their bound; max |err| "
+                                 f"{float(d[bad].max()):.3e}; idx {i.tolist()} gpu {gpu[i, ch].tolist()} "
+                                 f"ref {ref[i, ch].tolist()} gap {None if gap is None else gap[i].tolist()}")
+    flips = (np.abs(gpu[:, 4] - ref[:, 4]) > limit[4]) & assessed & near
     stats["flips"] = int(flips.sum())
     assert stats["flips"] <= stats["near"]
+    if stats["ill"]:
+        print(f"{label}: {stats['ill']} ill-conditioned cells (gap < {GAP_MIN:g}) checked against "
+              f"C_GAP u / gap, largest |error| / bound {stats['ill_ratio']:.3g}")
     return stats
 
 

@@ -78,6 +78,24 @@ def test_query_rejects_null_without_gpu(lib):
     assert rc == abi.SEB_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("change", [dict(length=30.0), dict(length=9.0, width=9.0, res=0.05), dict(n_yaw=3),
+                                    dict(length=4.0, width=3.0, res=0.05)])
+def test_noalloc_validates_like_the_allocating_query(lib, change):
+    """The allocation-free query builds its lattice through the same tables as seb_query_poses,
+    so both return the same status for parameter sets the tables reject (reach beyond the
+    packing, moments or staged tile too large, odd yaw count, a lattice above 256 points); the
+    checks run before any CUDA call."""
+    import ctypes
+
+    p = abi.seb_params_default()
+    for k, v in change.items():
+        setattr(p, k, v)
+    a = lib.seb_query_poses(ctypes.byref(p), 0x1000, 0, 0, 0x2000, 1, 0x3000, 0x4000, None, None)
+    b = lib.seb_query_poses_grad_noalloc(ctypes.byref(p), 0x1000, 0, 0, 0x2000, 1, 0x5000, 0x3000, 0x4000, 0x6000,
+                                         None)
+    assert a == b and a in (abi.SEB_ERR_BAD_SHAPE, abi.SEB_ERR_INVALID_ARG), (a, b)
+
+
 CONFIGS = [
     dict(nx=100, ny=100, n_yaw=36, res=0.1, length=0.6, width=0.4),
     dict(nx=400, ny=400, n_yaw=72, res=0.05, length=0.9, width=0.6),
@@ -237,6 +255,9 @@ def test_surrogate_argument_checks_without_gpu(lib):
     assert lib.seb_sur_forward(None, 1) == INV
     assert lib.seb_sur_train_step(None, 1, 1e-3, 1, None) == INV
     assert lib.seb_sur_infer(None, fake, 0.04, 3, 1, fake, fake, None) == INV
+    buf = ctypes.create_string_buffer(64)
+    assert lib.seb_sur_state_bytes(None) == 0 and lib.seb_sur_step(None) == -1
+    assert lib.seb_sur_save(None, buf, 64) == INV and lib.seb_sur_load(None, buf, 64) == INV
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

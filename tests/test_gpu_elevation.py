@@ -21,6 +21,9 @@ SIGMA_B = np.diag([0.01, 0.01, 0.01]) ** 2
 def seb():
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
     import paper_2503_02412_gb300 as seb
 
     return seb

@@ -16,6 +16,9 @@ pytestmark = pytest.mark.gpu
 def seb():
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
     import paper_2503_02412_gb300 as seb
 
     return seb

@@ -26,6 +26,9 @@ GRAD_RTOL = 1e-5  # plus FP32 rounding relative to the derivative itself
 def seb():
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
     import paper_2503_02412_gb300 as seb
 
     return seb

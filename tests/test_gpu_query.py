@@ -44,16 +44,32 @@ def test_forward_matches_oracle(seb, n):
     compare(g, gf, r, rf, label="query fwd")
 
 
+def _ambiguous_poses(seb, cfg, poses, origin=(0, 0), eps=1e-4):
+    """Poses with a lattice point whose grid coordinate lies within eps cells of a grid line:
+    there floor() of the FP32 coordinate may differ from the FP64 one, and with it the
+    point's bilinear cell (and whether that cell touches an unknown cell or the window edge)."""
+    lat = np.array(seb.abi.seb_footprint_table(seb.SebParams(**cfg).c(), 0), np.float64)
+    P = poses.astype(np.float32).astype(np.float64)
+    res = float(np.float32(cfg["res"]))
+    c, s = np.cos(P[:, 2:3]), np.sin(P[:, 2:3])
+    u = P[:, 0:1] / res - origin[0] - 0.5 + c * lat[:, 0] - s * lat[:, 1]
+    v = P[:, 1:2] / res - origin[1] - 0.5 + s * lat[:, 0] + c * lat[:, 1]
+    near = lambda t: np.abs(t - np.round(t)) < eps  # noqa: E731
+    return (near(u) | near(v)).any(axis=1)
+
+
 def test_forward_near_edges_and_unknown(seb):
     e = bumpy_plane(2)
     e[40:55, 40:60] = np.nan
     poses = random_poses(6, 4000, 100, 100, 0.1, -3)  # some poses partly outside the window
     g, gf = fwd(seb, C1, e, poses)
     r, rf = oracle.query_poses(oracle.OracleParams(**C1), e.astype(np.float64), poses.astype(np.float64))
-    # validity of a lattice point is decided by floor() of its grid coordinate: FP32 vs FP64
-    # can disagree only for points within ~1e-5 cells of a grid line next to an unknown cell
+    # the UNKNOWN bit may differ only where a lattice point sits on a grid line (FP32 vs FP64
+    # floor of its grid coordinate); every such pose must be one of those
     same = (gf & 1) == (rf & 1)
-    assert same.mean() > 0.999
+    amb = _ambiguous_poses(seb, C1, poses)
+    assert not (~same & ~amb).any(), np.flatnonzero(~same & ~amb)[:8]
+    print(f"UNKNOWN bit differs on {int((~same).sum())} of {int(amb.sum())} poses with a point on a grid line")
     compare(g[same], gf[same], r[same], rf[same], label="query edges")
     assert (gf & 1).sum() > 100
 
@@ -106,13 +122,18 @@ def test_backward_matches_oracle_adjoint(seb):
     g, out, fl = _bwd(seb, cfg, e, poses, gout)
     r = oracle.query_poses_vjp(oracle.OracleParams(**cfg), e.astype(np.float64), poses.astype(np.float64), gout)
     ok = (fl & 5) == 0
-    scale = np.abs(r).max(axis=0)
-    rel = np.abs(g - r) / (1e-3 * scale + np.abs(r))
     assert ok.mean() > 0.99
-    assert np.median(rel[ok]) < 1e-4
-    assert np.percentile(rel[ok], 99) < 1e-3 * 10
-    # absolute error relative to the gradient scale of each component
-    assert (np.abs(g - r)[ok] / scale).max() < 1e-3
+    # Element-wise: relative error <= 1e-3 wherever |g| is at least 1e-2 of the component's
+    # largest |g| over the batch; below that floor, absolute error <= 1e-3 of the floor (a
+    # relative bound there would ask FP32 for digits that cancellation in the adjoint removes).
+    scale = np.abs(r[ok]).max(axis=0)
+    floor = 1e-2 * scale
+    big = ok[:, None] & (np.abs(r) >= floor)
+    small = ok[:, None] & ~big
+    rel = np.abs(g - r) / np.maximum(np.abs(r), 1e-300)
+    assert big.mean() > 0.8
+    assert rel[big].max() <= 1e-3, rel[big].max()
+    assert (np.abs(g - r)[small] <= (1e-3 * floor * np.ones_like(r))[small]).all()
 
 
 def test_backward_default_thresholds_branches(seb):

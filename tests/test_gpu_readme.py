@@ -13,6 +13,9 @@ pytestmark = pytest.mark.gpu
 def test_quick_start_usage():
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
     import paper_2503_02412_gb300 as seb
     from paper_2503_02412_gb300.query import QueryPoses
 

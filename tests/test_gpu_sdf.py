@@ -20,6 +20,9 @@ TOL = 2e-6  # FP32 sqrt of an exact integer squared distance, times res
 def seb():
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
     import paper_2503_02412_gb300 as seb
 
     return seb

@@ -236,3 +236,55 @@ def test_training_gain_report(mods, record_property):
         record_property(k, v)
     print(res)
     assert res["bumpy_pitch_p50"] < 0.05 and res["bumpy_roll_p50"] < 0.05
+
+
+@pytest.mark.parametrize("engine", ["tcgen05", "simt"])
+def test_checkpoint_resume_repeats_the_run(mods, engine):
+    """seb_sur_save / seb_sur_load through the C ABI: train 3 steps, checkpoint (the C image
+    plus the caller's generator state), train 3 more; then restore the image into a fresh
+    handle initialised with other weights, restore the generator and train the same 3 steps.
+    Losses, weights and Adam state come out bit-identical (deterministic reductions)."""
+    seb, surrogate = mods
+
+    def fresh(seed):
+        s = surrogate.Surrogate(seb.SebParams(nx=96, ny=96, **C2), max_batch=64, world=160)
+        s.set_engine(engine)
+        s.init(seed)
+        return s
+
+    a = fresh(5)
+    rng = np.random.default_rng(77)
+    a.train_steps(rng, 0, 3, 6, batch=64, lr=3e-3)
+    ck = a.state_dict()
+    gen = rng.bit_generator.state
+    assert ck["step"] == 3 and seb.abi.seb_sur_step(a.handle) == 3
+    assert len(ck["image"]) == seb.abi.seb_sur_state_bytes(a.handle)
+    la = a.train_steps(rng, 3, 3, 6, batch=64, lr=3e-3, log_every=1)
+    end_a = a.state_dict()
+
+    b = fresh(6)
+    assert not torch.equal(b.master, a.master)
+    b.load_state_dict(ck)
+    assert b.step == 3
+    rng_b = np.random.default_rng()
+    rng_b.bit_generator.state = gen
+    lb = b.train_steps(rng_b, 3, 3, 6, batch=64, lr=3e-3, log_every=1)
+    end_b = b.state_dict()
+    assert [x[1] for x in la] == [x[1] for x in lb], (la, lb)
+    assert end_a["image"] == end_b["image"] and end_b["step"] == 6
+    assert torch.equal(a.master, b.master) and torch.equal(a.weights_bf16, b.weights_bf16)
+
+
+def test_checkpoint_rejects_other_networks(mods):
+    seb, surrogate = mods
+    a = surrogate.Surrogate(seb.SebParams(nx=96, ny=96, **C2), max_batch=4, world=64)
+    a.init(1)
+    img = a.state_dict()["image"]
+    other = surrogate.Surrogate(seb.SebParams(nx=96, ny=96, **dict(C2, n_yaw=36)), max_batch=4, world=64)
+    with pytest.raises(seb.abi.SebError) as ei:
+        seb.abi.seb_sur_load(other.handle, img)
+    assert ei.value.status == seb.abi.SEB_ERR_INVALID_ARG and "does not fit" in str(ei.value)
+    with pytest.raises(seb.abi.SebError):
+        seb.abi.seb_sur_load(a.handle, img[:1000])
+    with pytest.raises(seb.abi.SebError):
+        seb.abi.seb_sur_load(a.handle, b"X" * len(img))

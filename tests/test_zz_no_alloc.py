@@ -45,12 +45,10 @@ def noalloc(seb, p, te, tp, g, st):
     return out, fl, gp
 
 
-def test_noalloc_matches_allocating_query_twice(seb):
-    p = seb.SebParams(**C1).c()
-    te = torch.from_numpy(bumpy_plane(31)).cuda()
+def _compare_twice(seb, p, te, cases, origin=(3, -2)):
     st = torch.cuda.current_stream().cuda_stream
-    for seed, n in ((1, 5000), (2, 777)):  # the second call reuses the scratch of the first
-        tp = torch.from_numpy(random_poses(seed, n, 100, 100, 0.1, 3, origin=(3, -2))).cuda()
+    for seed, n in cases:  # each call reuses the scratch the previous one left
+        tp = torch.from_numpy(random_poses(seed, n, 100, 100, 0.1, 3, origin=origin)).cuda()
         g = torch.randn(n, 5, device="cuda", generator=torch.Generator("cuda").manual_seed(seed))
         ro, rf, rg = reference(seb, p, te, tp, g, st)
         no, nf, ng = noalloc(seb, p, te, tp, g, st)
@@ -60,6 +58,23 @@ def test_noalloc_matches_allocating_query_twice(seb):
         assert torch.equal(fin, torch.isfinite(no))
         assert torch.allclose(no[fin], ro[fin], rtol=1e-5, atol=1e-6)
         assert torch.allclose(ng, rg, rtol=1e-5, atol=1e-6)
+
+
+def test_noalloc_matches_allocating_query_twice(seb):
+    """Two calls in a row on the grouped kernels (fewer than 65,536 poses), then the largest
+    batch the scratch takes (65,536 poses: the one-pose-per-thread kernels, every record of the
+    array written and read) and a smaller batch after it."""
+    p = seb.SebParams(**C1).c()
+    te = torch.from_numpy(bumpy_plane(31)).cuda()
+    _compare_twice(seb, p, te, ((1, 5000), (2, 777), (3, 65536), (4, 1000)))
+
+
+def test_noalloc_ellipse_footprint(seb):
+    """The paper's elliptical footprint: the lattice comes from the same tables as the
+    allocating query's."""
+    p = seb.SebParams(**dict(C1, shape="ellipse", length=0.8, width=0.5)).c()
+    te = torch.from_numpy(bumpy_plane(33)).cuda()
+    _compare_twice(seb, p, te, ((5, 3000), (6, 65536)))
 
 
 def test_noalloc_rejects_batches_beyond_the_scratch(seb):
