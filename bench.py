@@ -120,15 +120,19 @@ def workload(seed=1):
     return world, origins
 
 
-def oracle_params():
+def oracle_params(**kw):
+    """Oracle parameters (a plain record of the assessment parameters) of the 400x400x72 map, or
+    of the given geometry.  The oracle's arithmetic runs only in the CPU-baseline leg."""
     import oracle
 
-    return oracle.OracleParams(nx=NX, ny=NY, n_yaw=K, res=RES, length=LENGTH, width=WIDTH)
+    return oracle.OracleParams(**(kw or dict(nx=NX, ny=NY, n_yaw=K, res=RES, length=LENGTH, width=WIDTH)))
 
 
-def cpu_baseline(world, origins, budget_s, rng_seed=0):
+def cpu_baseline(world, origins, budget_s, rng_seed=0, accuracy_jobs=None):
     """Times the FP64 oracle on a bounded random sample of the rebuild's cells: fresh random
-    draws, each sized by a short calibration to about a second, until budget_s has passed."""
+    draws, each sized by a short calibration to about a second, until budget_s has passed.
+    With accuracy_jobs, the same leg then runs the oracle on those fixed samples and reports the
+    GPU's error against it (accuracy_vs_oracle)."""
     import oracle
 
     oracle.build()
@@ -158,9 +162,40 @@ def cpu_baseline(world, origins, budget_s, rng_seed=0):
         total_t += time.perf_counter() - t0
         total_n += n
         draws += 1
-    return {"value": total_n / total_t, "unit": "SE(2) cells/s", "cores": cores, "kind": "oracle",
-            "sample": f"{total_n} random (c, r, k) cells of the 400x400x72 rebuild ({draws} draws of {n}), "
-                      f"FP64 brute force, {total_t:.2f} s"}
+    res = {"value": total_n / total_t, "unit": "SE(2) cells/s", "cores": cores, "kind": "oracle",
+           "sample": f"{total_n} random (c, r, k) cells of the 400x400x72 rebuild ({draws} draws of {n}), "
+                     f"FP64 brute force, {total_t:.2f} s"}
+    if accuracy_jobs:
+        res["accuracy"] = accuracy_vs_oracle(accuracy_jobs, cores)
+    return res
+
+
+def accuracy_vs_oracle(jobs, cores):
+    """Part of the CPU-baseline leg: runs the FP64 oracle on fixed samples of cells and reports
+    the error of the GPU outputs on them, per output channel (max and p99 |delta| over the
+    cells both sides assess; z in m, angles in rad), with the count of cells whose FP32
+    conditioning bound C_GAP u / (g n_z) exceeds 1e-4 (g the oracle's relative eigen-gap).
+    jobs: {label: (geometry dict, elevation [ny][nx] float64, cells [n][3] (c, r, k), origin,
+    gpu outputs [n][5], gpu flags [n])}."""
+    import oracle
+
+    u32, c_gap = 2.0 ** -24, 16.0
+    out = {}
+    for label, (geom, elev, cells, origin, g, gf) in jobs.items():
+        r, rf, gap = oracle.assess_cells(oracle_params(**geom), elev, cells, origin, n_threads=cores)
+        ok = ((rf & 5) == 0) & ((gf & 5) == 0)
+        d = np.abs(g[ok].astype(np.float64) - r[ok])
+        with np.errstate(invalid="ignore", divide="ignore"):
+            sp, sr = np.sin(r[ok, 1]), np.sin(r[ok, 2])
+            nz = np.sqrt(np.clip(1 - sp * sp - sr * sr, 1e-12, 1))
+            ill = int((c_gap * u32 / (gap[ok] * nz) > 1e-4).sum())
+        row = {"cells": int(len(cells)), "assessed_both": int(ok.sum()), "ill_conditioned": ill,
+               "unknown_bits_equal": bool(np.array_equal(rf & 1, gf & 1))}
+        for ch, name in enumerate(("z", "pitch", "roll", "rough", "risk")):
+            row[name] = {"max": float(d[:, ch].max()) if d.size else None,
+                         "p99": float(np.percentile(d[:, ch], 99)) if d.size else None}
+        out[label] = row
+    return out
 
 
 class Clocks:
@@ -475,10 +510,35 @@ def main():
     peak = sms * 128 * 2 * 2070e6 / 1e12  # FP32 lanes x FMA x max SM clock
     traffic = NCU_TRAFFIC["bytes"] if NCU_TRAFFIC["sources_sha"] == kernel_sources_sha() else None
 
+    # the whole step against the same peak: the rebuild's FLOP plus those of every cell the 50
+    # moves recompute (each recomputed (x, y) cell takes all K yaws, i.e. sum over the pairs)
+    flop_xy = sum(algorithmic_flop_per_cell(t) for t in tables)  # one (x, y) cell, all yaw pairs
+    cells_per_step = cells_total // args.steps
+    step_flop = cells_per_step / K * flop_xy
+    shift_flop = (cells_per_step - NX * NY * K) / K * flop_xy / N_SHIFTS
+    shift_us = (ms_per_step - rb) / N_SHIFTS * 1e3
+
+    # the rolled map after the 50 separate shifts above, sampled for the oracle comparison of the
+    # CPU-baseline leg (rolling is bit-identical to a rebuild, so this is also the rebuild's error)
+    acc_jobs = {}
+    if rank == 0 and world_size == 1 and not args.no_cpu_baseline:
+        out_l, fl_l = m.outputs()
+        rng = np.random.default_rng(11)
+        ns = 1_000_000
+        cs = np.stack([rng.integers(0, NX, ns), rng.integers(0, NY, ns), rng.integers(0, K, ns)], 1).astype(np.int32)
+        cti = torch.from_numpy(cs.astype(np.int64)).to(dev)
+        g = out_l[:, cti[:, 2], cti[:, 1], cti[:, 0]].T.contiguous().cpu().numpy()
+        gf = fl_l[cti[:, 2], cti[:, 1], cti[:, 0]].cpu().numpy()
+        of = origins[-1]
+        acc_jobs["400x400x72_after_50_shifts"] = (
+            dict(nx=NX, ny=NY, n_yaw=K, res=RES, length=LENGTH, width=WIDTH),
+            world_np[of[1]:of[1] + NY, of[0]:of[0] + NX].astype(np.float64), cs, tuple(of), g, gf)
+        del out_l, fl_l
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(seb, m, world_np, origins, args, dev)
-    rows = None if args.no_rows or world_size > 1 else measure_rows(seb, args, dev)
+    rows = None if args.no_rows or world_size > 1 else measure_rows(seb, args, dev, acc_jobs)
     line = {
         "metric": METRIC,
         "value": value, "unit": "SE(2) cells/s", "n_gpus": world_size, "steps": args.steps,
@@ -497,7 +557,14 @@ def main():
                      "flop_basis": "algorithmic: 9 N + 200 per cell and yaw pair (N footprint points)",
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x 2070 MHz",
                      "executed": {"flop_per_launch": flop_exec, "achieved": achieved_exec, "frac": achieved_exec / peak,
-                                  "flop_basis": "sliding row sums as run: 1.5 N + 15.5 R + 200 per cell and yaw pair"}},
+                                  "flop_basis": "sliding row sums as run: 1.5 N + 15.5 R + 200 per cell and yaw pair"},
+                     "step": {"flop": step_flop, "achieved": step_flop / (ms_per_step * 1e-3) / 1e12,
+                              "frac": step_flop / (ms_per_step * 1e-3) / 1e12 / peak,
+                              "basis": "rebuild + 50 shifts in one batch: recomputed cells x the same per-cell FLOP"},
+                     "shift": {"flop_mean": shift_flop, "us_mean": shift_us,
+                               "achieved": shift_flop / (shift_us * 1e-6) / 1e12,
+                               "frac": shift_flop / (shift_us * 1e-6) / 1e12 / peak,
+                               "basis": "one 10-cell move of the batch: band cells x the same per-cell FLOP"}},
         "gpu_launches": launches, "fp64_solves": n64, "degenerate": ndeg, "clocks": clk,
     }
     if e2e is not None:
@@ -505,7 +572,8 @@ def main():
     if rows is not None:
         line["rows"] = rows
     if rank == 0 and world_size == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(world_np, origins, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(world_np, origins, args.cpu_seconds, accuracy_jobs=acc_jobs)
+        line["accuracy"] = line["cpu_baseline"].pop("accuracy", None)
     if rank == 0:
         print(json.dumps(line))
     if world_size > 1:
@@ -526,7 +594,7 @@ def _time(fn, reps, stream):
     return e0.elapsed_time(e1) / reps
 
 
-def measure_rows(seb, args, dev):
+def measure_rows(seb, args, dev, acc_jobs=None):
     """The other rows of the hot path, each on its own configuration, outside the timed step:
     continuous-pose query forward / backward (1,048,576 poses on the 100x100 map), the
     reduced-precision rebuild (1024x1024x72, FP32 / BF16 / FP16 elevation) and the learned
@@ -615,22 +683,43 @@ def measure_rows(seb, args, dev):
                                "config": "fractal map with 5 % NaN discs, unbounded nearest-neighbour filling"}
     del mc2, sdf_t, work, p2, v2, g2, sdf_grid, risk, e2, filled, iw
     rows["local_mapping_cycle_180x180x30"] = local_mapping_cycle(seb, dev, st)
-    # S8
-    e3 = torch.from_numpy(bumpy_plane(21, 1024, 1024, 0.05)).to(dev)
+    # S8: every storage / summation form on the 1024 x 1024 x 72 map, timed, and its outputs on a
+    # fixed sample of 20,000 cells kept for the oracle comparison of the CPU-baseline leg (against
+    # the unquantised FP64 terrain: the whole error of the form; and against the heights the form
+    # stores: the arithmetic's share)
+    e3_64 = bumpy_plane(21, 1024, 1024, 0.05, dtype=np.float64)
+    e3 = torch.from_numpy(e3_64.astype(np.float32)).to(dev)
+    rng = np.random.default_rng(4)
+    cells3 = np.stack([rng.integers(0, 1024, 20000), rng.integers(0, 1024, 20000), rng.integers(0, 72, 20000)],
+                      1).astype(np.int32)
+    ci = torch.from_numpy(cells3.astype(np.int64)).to(dev)
     prec = {}
-    for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16), ("f16", torch.float16)):
-        m = seb.SebMap(seb.SebParams(nx=1024, ny=1024, n_yaw=72, res=0.05, length=0.9, width=0.6, elev_dtype=dt), dev)
-        ed = e3.to(dt)
+    C3 = dict(nx=1024, ny=1024, n_yaw=72, res=0.05, length=0.9, width=0.6)
+    forms = (("f32", dict(elev_dtype=torch.float32), e3),
+             ("bf16", dict(elev_dtype=torch.bfloat16), e3.to(torch.bfloat16)),
+             ("f16", dict(elev_dtype=torch.float16), e3.to(torch.float16)),
+             ("bf16_tiled", dict(elev_dtype="bf16_tiled"), seb.encode_bf16_tiled(e3)),
+             ("f32_compensated", dict(precision="compensated"), e3))
+    for name, kw, ed in forms:
+        m = seb.SebMap(seb.SebParams(**C3, **kw), dev)
         t = _time(lambda: m.update(ed), 5, st)
         prec[name] = {"rebuild_ms": t, "cells_per_s": 1024 * 1024 * 72 / t * 1e3}
+        g = m.out_phys[:, ci[:, 2], ci[:, 1], ci[:, 0]].T.contiguous().cpu().numpy()
+        gf = m.flags_phys[ci[:, 2], ci[:, 1], ci[:, 0]].cpu().numpy()
+        if acc_jobs is not None:
+            op = dict(C3)  # the oracle's parameters are built in the CPU-baseline leg
+            acc_jobs[f"1024x1024x72_{name}_vs_fp64_terrain"] = (op, e3_64, cells3, (0, 0), g, gf)
+            if name in ("bf16", "f16"):
+                stored = ed.float().cpu().numpy().astype(np.float64)
+                acc_jobs[f"1024x1024x72_{name}_vs_stored_heights"] = (op, stored, cells3, (0, 0), g, gf)
+            elif name == "bf16_tiled":
+                d, b = seb.tiled_parts(ed, 1024, 1024)
+                idx = np.arange(1024) // 16
+                stored = (b.cpu().numpy()[idx][:, idx] + d.float().cpu().numpy()).astype(np.float32)
+                acc_jobs[f"1024x1024x72_{name}_vs_stored_heights"] = (op, stored.astype(np.float64), cells3, (0, 0), g,
+                                                                      gf)
         del m
         torch.cuda.empty_cache()
-    mc = seb.SebMap(seb.SebParams(nx=1024, ny=1024, n_yaw=72, res=0.05, length=0.9, width=0.6,
-                                  precision="compensated"), dev)
-    t = _time(lambda: mc.update(e3), 5, st)
-    prec["f32_compensated"] = {"rebuild_ms": t, "cells_per_s": 1024 * 1024 * 72 / t * 1e3}
-    del mc
-    torch.cuda.empty_cache()
     rows["precision_1024x1024x72"] = prec
     # S11 / S12
     C2 = dict(nx=NX, ny=NY, n_yaw=K, res=RES, length=LENGTH, width=WIDTH)

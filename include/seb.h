@@ -55,6 +55,14 @@ extern "C" {
 #define SEB_F32 0
 #define SEB_BF16 1
 #define SEB_F16 2
+/* BF16 height offsets from an FP32 base per 16 x 16 world-aligned tile: a window's buffer holds
+ * the BF16 offsets [ny][nx] (logical order), then, at byte offset seb_tiled_base_offset(nx, ny),
+ * the FP32 bases [TY][TX], TX = (nx + 15) / 16 + 1, TY = (ny + 15) / 16 + 1.  Cell (c, r) of a
+ * window at origin (o_i, o_j) has the height base[(r + py) / 16][(c + px) / 16] + offset[r][c]
+ * (FP32 sum), px = o_i mod 16, py = o_j mod 16 (0..15): the base belongs to the world tile of the
+ * cell, so windows cut from one encoding of a world agree cell by cell.  Maps only (the
+ * continuous query and the surrogate read FP32/BF16/FP16 heights). */
+#define SEB_BF16_TILED 3
 
 /* Moment accumulation. */
 #define SEB_PLAIN_F32 0   /* FP32 sums about the footprint's reference height */
@@ -91,7 +99,7 @@ typedef struct {
   float phi_y_max;    /* lateral tilt limit, rad (default 0.52, Sec. VII-B) */
   float w[3];         /* risk weights for (kappa, |pitch|, |roll|) ratios (default 1/3 each) */
   int32_t n_min;      /* minimum known footprint cells; 0 = max(3, ceil(N_k / 2)) per bin */
-  int32_t elev_dtype; /* SEB_F32 | SEB_BF16 | SEB_F16 */
+  int32_t elev_dtype; /* SEB_F32 | SEB_BF16 | SEB_F16 | SEB_BF16_TILED */
   int32_t precision;  /* SEB_PLAIN_F32 | SEB_COMPENSATED */
   float gap_fp64;     /* relative eigen-gap (lambda_mid - lambda_min) / trace below which the
                          covariance and eigen-solve are redone in FP64 (default 1e-2) */
@@ -129,6 +137,22 @@ int seb_footprint_table(const seb_params* p, int32_t k, int32_t* di, int32_t* dj
 /* Bytes of device workspace a map needs: the SoA outputs, the flags and a small control
  * block (the device error word and counters). */
 size_t seb_workspace_bytes(const seb_params* p);
+
+/* Bytes of one elevation window of p->nx x p->ny cells in p->elev_dtype (0 for bad params), and
+ * the byte offset of the bases in a SEB_BF16_TILED window (the BF16 offsets rounded up to 256). */
+size_t seb_window_bytes(const seb_params* p);
+size_t seb_tiled_base_offset(int32_t nx, int32_t ny);
+
+/*
+ * Encodes an FP32 elevation window (device [ny][nx], NaN = unknown, logical order, origin
+ * (origin_i, origin_j)) as a SEB_BF16_TILED window in out_dev (device, 256-byte aligned,
+ * seb_window_bytes bytes): per 16 x 16 world-aligned tile the base is the midpoint of the tile's
+ * smallest and largest known height (0 without one), and each offset is the BF16 value nearest
+ * to height - base (NaN stays NaN).  Encode a whole world once and cut windows from it when maps
+ * roll: re-encoding each window gives tiles cut by the window edge other bases.
+ */
+int seb_encode_bf16_tiled(const float* elev_dev, int32_t nx, int32_t ny, int64_t origin_i, int64_t origin_j,
+                          void* out_dev, seb_stream_t stream);
 
 /*
  * Creates a map over caller-owned device workspace (>= seb_workspace_bytes, 256-byte

@@ -21,7 +21,7 @@ SEB_ERR_DEVICE_FAULT = -5
 SEB_ERR_WORKSPACE = -6
 
 SEB_RECT, SEB_ELLIPSE = 0, 1
-SEB_F32, SEB_BF16, SEB_F16 = 0, 1, 2
+SEB_F32, SEB_BF16, SEB_F16, SEB_BF16_TILED = 0, 1, 2, 3
 SEB_PLAIN_F32, SEB_COMPENSATED = 0, 1
 SEB_FLAG_UNKNOWN, SEB_FLAG_OBSTACLE, SEB_FLAG_DEGENERATE, SEB_FLAG_FP64 = 1, 2, 4, 8
 SEB_FLAG_SURROGATE = 16
@@ -37,6 +37,9 @@ EXPORTS = (
     "seb_last_error",
     "seb_footprint_table",
     "seb_workspace_bytes",
+    "seb_window_bytes",
+    "seb_tiled_base_offset",
+    "seb_encode_bf16_tiled",
     "seb_map_create",
     "seb_map_destroy",
     "seb_map_set_stream",
@@ -211,6 +214,9 @@ def load():
             "seb_last_error": (ctypes.c_char_p, [vp]),
             "seb_footprint_table": (ctypes.c_int, [P, i32, i32p, i32p, i32]),
             "seb_workspace_bytes": (sz, [P]),
+            "seb_window_bytes": (sz, [P]),
+            "seb_tiled_base_offset": (sz, [i32, i32]),
+            "seb_encode_bf16_tiled": (ctypes.c_int, [vp, i32, i32, i64, i64, vp, vp]),
             "seb_map_create": (ctypes.c_int, [P, vp, sz, vp, ctypes.POINTER(vp)]),
             "seb_map_destroy": (ctypes.c_int, [vp]),
             "seb_map_set_stream": (ctypes.c_int, [vp, vp]),
@@ -301,6 +307,18 @@ def seb_footprint_table(p: seb_params, k: int):
 
 def seb_workspace_bytes(p: seb_params) -> int:
     return int(load().seb_workspace_bytes(ctypes.byref(p)))
+
+
+def seb_window_bytes(p: seb_params) -> int:
+    return int(load().seb_window_bytes(ctypes.byref(p)))
+
+
+def seb_tiled_base_offset(nx: int, ny: int) -> int:
+    return int(load().seb_tiled_base_offset(nx, ny))
+
+
+def seb_encode_bf16_tiled(elev_ptr, nx, ny, origin_i, origin_j, out_ptr, stream=0) -> None:
+    _check(load().seb_encode_bf16_tiled(elev_ptr, nx, ny, origin_i, origin_j, out_ptr, stream))
 
 
 def seb_map_create(p: seb_params, workspace_ptr: int, nbytes: int, stream: int = 0) -> int:

@@ -79,6 +79,11 @@ static Launch base_launch(const seb_map* m, const void* elev) {
   Launch L;
   launch_defaults(m->p, m->T, &L);
   L.elev = elev;
+  if (m->p.elev_dtype == SEB_BF16_TILED && elev) {
+    L.tile_base = reinterpret_cast<const float*>(static_cast<const uint8_t*>(elev) +
+                                                 tiled_base_offset(m->p.nx, m->p.ny));
+    L.base_tx = tiled_tx(m->p.nx);
+  }
   L.ring_x = m->ring_x;
   L.ring_y = m->ring_y;
   L.out = m->out;
@@ -96,6 +101,8 @@ void launch_request(Launch& L, int x0, int y0, int w, int h) {
 void launch_set_origin(Launch& L, int64_t oi, int64_t oj) {
   L.phase_x = (int32_t)(((oi % 4) + 4) % 4);
   L.phase_y = (int32_t)(((oj % 2) + 2) % 2);
+  L.base_px = (int32_t)(((oi % kBaseTile) + kBaseTile) % kBaseTile);
+  L.base_py = (int32_t)(((oj % kBaseTile) + kBaseTile) % kBaseTile);
 }
 
 static int64_t rect_cells(const Launch& L, int n_yaw) {
@@ -164,6 +171,22 @@ size_t seb_workspace_bytes(const seb_params* p) {
   SEB_RANGE();
   if (!p || validate_params(*p) != SEB_OK) return 0;
   return kControlBytes + align256(out_bytes(*p)) + align256(flags_bytes(*p));
+}
+
+size_t seb_tiled_base_offset(int32_t nx, int32_t ny) {
+  if (nx < 1 || ny < 1) return 0;
+  return tiled_base_offset(nx, ny);
+}
+
+size_t seb_window_bytes(const seb_params* p) {
+  if (!p || validate_params(*p) != SEB_OK) return 0;
+  const size_t n = (size_t)p->nx * p->ny;
+  switch (p->elev_dtype) {
+    case SEB_F32: return n * 4;
+    case SEB_BF16:
+    case SEB_F16: return n * 2;
+    default: return tiled_base_offset(p->nx, p->ny) + (size_t)tiled_tx(p->nx) * tiled_tx(p->ny) * 4;
+  }
 }
 
 int seb_map_create(const seb_params* p, void* ws, size_t bytes, seb_stream_t stream, seb_map** out) {
@@ -287,6 +310,7 @@ static int shift_impl(seb_map* m, const void* elev, int64_t oi, int64_t oj, int 
   if (left + right >= nx || top + bottom >= ny) {
     launch_request(L, 0, 0, nx, ny);
   } else {
+    L.all_masked = 1;  // bands along the window edge (the results do not depend on this choice)
     launch_request(L, 0, 0, left, ny);
     launch_request(L, nx - right, 0, right, ny);
     launch_request(L, left, 0, nx - left - right, top);

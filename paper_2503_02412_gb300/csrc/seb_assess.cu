@@ -23,12 +23,49 @@
 // relative eigen-gap below gap_fp64 redoes the eigen-solve in FP64.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cudaTypedefs.h>
+#include <string.h>
+
+#include <mutex>
+#include <type_traits>
 
 #include "seb_device.cuh"
 #include "seb_internal.h"
 
 namespace seb {
+
+// Element tag of SEB_BF16_TILED windows: a BF16 offset from the FP32 base of its 16 x 16 tile.
+struct Bf16Tiled {
+  __nv_bfloat16 v;
+};
+template <>
+__device__ __forceinline__ float to_f32<Bf16Tiled>(Bf16Tiled v) {
+  return __bfloat162float(v.v);
+}
+
 namespace {
+
+// Height of in-window cell (gx, gy) of the launch's elevation window.
+template <typename E>
+__device__ __forceinline__ float load_elev(const Launch& L, int gx, int gy) {
+  return to_f32<E>(static_cast<const E*>(L.elev)[(int64_t)gy * L.nx + gx]);
+}
+template <>
+__device__ __forceinline__ float load_elev<Bf16Tiled>(const Launch& L, int gx, int gy) {
+  const float base = __ldg(&L.tile_base[((gy + L.base_py) >> 4) * L.base_tx + ((gx + L.base_px) >> 4)]);
+  return base + to_f32<Bf16Tiled>(static_cast<const Bf16Tiled*>(L.elev)[(int64_t)gy * L.nx + gx]);
+}
+// Height from a staged raw element of cell (gx, gy) (out of the window: the raw value is NaN).
+template <typename E>
+__device__ __forceinline__ float stage_elev(const Launch& L, E raw, int gx, int gy) {
+  return to_f32<E>(raw);
+}
+template <>
+__device__ __forceinline__ float stage_elev<Bf16Tiled>(const Launch& L, Bf16Tiled raw, int gx, int gy) {
+  const float d = to_f32<Bf16Tiled>(raw);
+  if (gx < 0 || gx >= L.nx || gy < 0 || gy >= L.ny) return d;
+  return __ldg(&L.tile_base[((gy + L.base_py) >> 4) * L.base_tx + ((gx + L.base_px) >> 4)]) + d;
+}
 
 // Algorithm 1 from the moments on: covariance, normal, roughness, frame (Eqs. 2-3),
 // pitch/roll at heading (ct, st), fitted-plane height at the cell centre, risk.
@@ -310,7 +347,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int row = idx / sw, col = idx - row * sw;
     const int gy = ty0 - ry + row, gx = tx0 - rx + col;
     float v = qnan;
-    if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) v = to_f32<E>(elev[(int64_t)gy * L.nx + gx]);
+    if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) v = load_elev<E>(L, gx, gy);
     if (v != v) rowflag[row] = 1;
     tile[idx] = v;
   }
@@ -417,9 +454,35 @@ __host__ __device__ inline int sl_sw2(int lay, int rx) { return (sl_tw(lay) + 2 
 __device__ __forceinline__ int sl_index(int r, int c, int sw2) { return r * sw2 + c + ((r >> 1) & 3); }
 constexpr int kSlQ = 6 * 4;  // missing-point moments per thread: [k][g] float2 (rows packed)
 
-template <typename E>
+// Tensor maps of the elevation for the TMA staging, one per tile layout (index stage_map()).
+struct alignas(64) StageMaps {
+  CUtensorMap map[3];
+};
+__host__ __device__ inline int stage_map(int lay) { return lay == 2 ? 0 : (lay == 3 ? 1 : 2); }
+// Width of the TMA box of a layout: the staged width plus the slack of rounding the box's first
+// column down to a multiple of q = 16 bytes / element size, rounded up to a multiple of q.
+__host__ __device__ inline int stage_box_w(int lay, int rx, int q) {
+  return (sl_tw(lay) + 2 * rx + q - 1 + q - 1) / q * q;
+}
+constexpr int kStageWaitPolls = 1 << 20;  // bounded wait for the staged tile
+
+// Kahan's compensated step (W. Kahan, "Further remarks on reducing truncation errors", CACM 8(1),
+// 1965) on packed pairs: s - c tracks the sum of the added terms (c holds minus the low-order
+// part the last additions lost).
+__device__ __forceinline__ void kadd2(float2& s, float2& c, float2 x) {
+  const float2 y = add2(x, neg2(c));
+  const float2 t = add2(s, y);
+  c = add2(add2(t, neg2(s)), neg2(y));
+  s = t;
+}
+
+// COMP (SEB_COMPENSATED): every accumulation over the row runs (the column-0 sums and the slide
+// differences) is Kahan-compensated; the sums within one run (at most ~20 terms of one row) stay
+// plain FP32.
+template <typename E, bool COMP>
 __global__ void __launch_bounds__(kThreads, 2)
-    assess_kernel_sl(const __grid_constant__ Tables T, const __grid_constant__ Launch L) {
+    assess_kernel_sl(const __grid_constant__ Tables T, const __grid_constant__ Launch L,
+                     const __grid_constant__ StageMaps SM) {
   extern __shared__ float smem[];
   int* rowflag = reinterpret_cast<int*>(smem);
   float2* qs = reinterpret_cast<float2*>(smem + kMaxStageRows);  // [kSlQ][kThreads]
@@ -451,22 +514,49 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int sw = tw + 2 * rx, sh = th + 2 * ry, sw2 = sl_sw2(lay, rx);
   const int tid = threadIdx.x;
 
-  for (int i = tid; i < sh; i += kThreads) rowflag[i] = 0;
-  for (int i = tid; i < kSlQ * kThreads; i += kThreads) qs[i] = make_float2(0.f, 0.f);
-  __syncthreads();
   const E* __restrict__ elev = static_cast<const E*>(L.elev);
   const float qnan = __int_as_float(0x7fc00000);
-  {
-    // row-major walk of the staged tile in steps of kThreads cells (dc < sw, so one carry)
-    const int dr = kThreads / sw, dc = kThreads - dr * sw;
+  // Each staged value v goes to two vertical pairs: (row, row + 1).x and (row - 1, row).y.
+  auto put = [&](int row, int col, float v) {
+    if (v != v) rowflag[row] = 1;
+    if (row < sh - 1) pt[sl_index(row, col, sw2)].x = v;
+    if (row > 0) pt[sl_index(row - 1, col, sw2)].y = v;
+  };
+  const int dr = kThreads / sw, dc = kThreads - dr * sw;  // row-major walk in steps of kThreads cells
+  if (L.tma) {
+    // Tile + halo in one TMA copy into the CTA's shared memory (Algorithm 1's footprint cells
+    // of every cell of the tile; outside the window the map's fill value NaN = unknown, as in
+    // Sec. V-A).  The box starts at the staged tile's first column rounded down to 16 bytes and
+    // lands in the moment scratch qs, which is zeroed only after the repack below.
+    constexpr int q = 16 / (int)sizeof(E);
+    const int gx0 = tx0 - rx, gy0 = ty0 - ry;
+    const int x0a = gx0 >= 0 ? gx0 / q * q : -((q - 1 - gx0) / q) * q;
+    const int ox = gx0 - x0a, bw = stage_box_w(lay, rx, q);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(pt + (size_t)(sh - 1) * sw2);
+    const uint32_t base = smem_addr(qs);
+    const E* box = reinterpret_cast<const E*>(reinterpret_cast<char*>(qs) + (((base + 1023u) & ~1023u) - base));
+    if (tid == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (tid == 0) {
+      mbar_arrive_expect_tx(bar, (uint32_t)(bw * sh * (int)sizeof(E)));
+      tma_load_2d(const_cast<E*>(box), &SM.map[stage_map(lay)], x0a, gy0, bar);
+    }
+    for (int i = tid; i < sh; i += kThreads) rowflag[i] = 0;
+    const bool ok = mbar_wait_bounded(bar, 0, kStageWaitPolls);
+    if (__syncthreads_or(!ok)) {
+      // the copy did not land in time: report it, give the copy one more bounded wait (it
+      // writes this CTA's shared memory) and leave the tile unassessed
+      if (tid == 0) {
+        atomicOr(L.err, kErrStageTimeout);
+        mbar_wait_bounded(bar, 0, kStageWaitPolls);
+      }
+      __syncthreads();
+      if (L.early) asm volatile("griddepcontrol.wait;" ::: "memory");
+      return;
+    }
     int row = tid / sw, col = tid - (tid / sw) * sw;
     while (row < sh) {
-      const int gy = ty0 - ry + row, gx = tx0 - rx + col;
-      float v = qnan;
-      if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) v = to_f32<E>(elev[(int64_t)gy * L.nx + gx]);
-      if (v != v) rowflag[row] = 1;
-      if (row < sh - 1) pt[sl_index(row, col, sw2)].x = v;
-      if (row > 0) pt[sl_index(row - 1, col, sw2)].y = v;
+      put(row, col, stage_elev<E>(L, box[row * bw + ox + col], gx0 + col, gy0 + row));
       row += dr;
       col += dc;
       if (col >= sw) {
@@ -474,8 +564,29 @@ __global__ void __launch_bounds__(kThreads, 2)
         ++row;
       }
     }
+    __syncthreads();
+    if (tid == 0) mbar_inval(bar);
+    for (int i = tid; i < kSlQ * kThreads; i += kThreads) qs[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+  } else {
+    for (int i = tid; i < sh; i += kThreads) rowflag[i] = 0;
+    for (int i = tid; i < kSlQ * kThreads; i += kThreads) qs[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    int row = tid / sw, col = tid - (tid / sw) * sw;
+    while (row < sh) {
+      const int gy = ty0 - ry + row, gx = tx0 - rx + col;
+      float v = qnan;
+      if (gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny) v = load_elev<E>(L, gx, gy);
+      put(row, col, v);
+      row += dr;
+      col += dc;
+      if (col >= sw) {
+        col -= sw;
+        ++row;
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
 
   // block (cb, rp) of this thread: a half-warp holds 4 blocks x 4 pair rows
   const int cbs = 1 << lay, c4 = cbs >> 2;
@@ -519,15 +630,20 @@ __global__ void __launch_bounds__(kThreads, 2)
   // Column g is then column 0 plus the slides 1..g; its x-offsets are di = p - g.
   float2 S0c = zero2, S1c = zero2, S2c = zero2, S3c = zero2;
   float2 D0[3], D1[3], D2[3], D3[3];
+  float2 K0 = zero2, K1 = zero2, K2 = zero2, K3 = zero2;  // compensations (COMP)
+  float2 E0[3], E1[3], E2[3], E3[3];
 #pragma unroll
-  for (int t = 0; t < 3; ++t) D0[t] = D1[t] = D2[t] = D3[t] = zero2;
+  for (int t = 0; t < 3; ++t) D0[t] = D1[t] = D2[t] = D3[t] = E0[t] = E1[t] = E2[t] = E3[t] = zero2;
   auto Qs = [&](int k, int g) -> float2& { return qs[(k * 4 + g) * kThreads + tid]; };
 
   for (int q = r0; q < r1; ++q) {
     const uint32_t pk = T.runs[q];
     const int dj = unpack(pk, 0), lo = unpack(pk, 8), hi = unpack(pk, 16);
     const int row = ry + ly + dj;
-    const bool masked = __any_sync(0xffffffffu, rowflag[row] | rowflag[row + 1]);
+    // The masked path gives bit-identical sums for runs without unknown cells, so the choice is
+    // free: band tiles of a rolling shift touch the window edge, where nearly every run holds an
+    // unknown cell, and there the per-run vote costs more than it saves.
+    const bool masked = L.all_masked || __any_sync(0xffffffffu, rowflag[row] | rowflag[row + 1]);
     const float2* pq = pt + sl_index(row, rx + lx + lo, sw2);  // pq[k]: column lo + k of the block
     const int len = hi - lo + 1;
     const float flo = (float)lo, fhi = (float)hi;
@@ -535,16 +651,30 @@ __global__ void __launch_bounds__(kThreads, 2)
     auto slide = [&](int t, float2 zo, float2 zi) {
       const float po = flo + (float)t, pi = fhi + (float)(t + 1);
       const float2 d = add2(zi, neg2(zo));
-      D0[t] = add2(D0[t], d);
-      D2[t] = fma2(dj2, d, D2[t]);
-      D1[t] = fma2(f2(pi, pi), zi, fma2(f2(-po, -po), zo, D1[t]));
-      D3[t] = fma2(zi, zi, fma2(neg2(zo), zo, D3[t]));
+      if (COMP) {
+        kadd2(D0[t], E0[t], d);
+        kadd2(D2[t], E2[t], __fmul2_rn(dj2, d));
+        kadd2(D1[t], E1[t], fma2(f2(pi, pi), zi, __fmul2_rn(f2(-po, -po), zo)));
+        kadd2(D3[t], E3[t], fma2(zi, zi, __fmul2_rn(neg2(zo), zo)));
+      } else {
+        D0[t] = add2(D0[t], d);
+        D2[t] = fma2(dj2, d, D2[t]);
+        D1[t] = fma2(f2(pi, pi), zi, fma2(f2(-po, -po), zo, D1[t]));
+        D3[t] = fma2(zi, zi, fma2(neg2(zo), zo, D3[t]));
+      }
     };
     auto column0 = [&](float2 Ab, float2 Bx, float2 Cb) {
-      S0c = add2(S0c, Ab);
-      S1c = add2(S1c, Bx);
-      S2c = fma2(dj2, Ab, S2c);
-      S3c = add2(S3c, Cb);
+      if (COMP) {
+        kadd2(S0c, K0, Ab);
+        kadd2(S1c, K1, Bx);
+        kadd2(S2c, K2, __fmul2_rn(dj2, Ab));
+        kadd2(S3c, K3, Cb);
+      } else {
+        S0c = add2(S0c, Ab);
+        S1c = add2(S1c, Bx);
+        S2c = fma2(dj2, Ab, S2c);
+        S3c = add2(S3c, Cb);
+      }
     };
     // Column 0 of the block: A = sum z', C = sum z'^2 and Tb = sum of the running sums of z'
     // = sum (len - k) z'_k, so that sum p z' = (hi + 1) A - Tb with p = lo + k.
@@ -625,6 +755,19 @@ __global__ void __launch_bounds__(kThreads, 2)
         Qs(4, g) = fma2(dj2, sdi, Qs(4, g));
         Qs(5, g) = fma2(dj22, qn, Qs(5, g));
       }
+    }
+  }
+  if (COMP) {  // fold the compensations in: the exact sum is s - c
+    S0c = add2(S0c, neg2(K0));
+    S1c = add2(S1c, neg2(K1));
+    S2c = add2(S2c, neg2(K2));
+    S3c = add2(S3c, neg2(K3));
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      D0[t] = add2(D0[t], neg2(E0[t]));
+      D1[t] = add2(D1[t], neg2(E1[t]));
+      D2[t] = add2(D2[t], neg2(E2[t]));
+      D3[t] = add2(D3[t], neg2(E3[t]));
     }
   }
   float2 S0[4], S1[4], S2[4], S3[4];
@@ -805,13 +948,62 @@ size_t smem_sl(const Tables& T, const Launch& L) {
     const size_t s = (size_t)(sl_th(lay) + 2 * T.ry - 1) * sl_sw2(lay, T.rx);
     pairs = s > pairs ? s : pairs;
   }
-  return kMaxStageRows * sizeof(float) + ((size_t)kSlQ * kThreads + pairs) * sizeof(float2);
+  return kMaxStageRows * sizeof(float) + ((size_t)kSlQ * kThreads + pairs) * sizeof(float2) + 16;  // + mbarrier
+}
+
+// Driver entry point of cuTensorMapEncodeTiled (no link against libcuda), looked up once.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor maps for the TMA staging of every layout in the launch; false (plain loads) when the
+// elevation's rows are not 16-byte multiples, a box exceeds 256 elements per side or the moment
+// scratch it lands in, or the driver has no encoder.
+template <typename E>
+bool stage_maps(const Tables& T, const Launch& L, StageMaps* M) {
+  constexpr int es = (int)sizeof(E), q = 16 / es;
+  if (((size_t)L.nx * es) % 16 != 0 || ((uintptr_t)L.elev % 16) != 0) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const CUtensorMapDataType dt = es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                         : (sizeof(E) == 2 && std::is_same<E, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                                             : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+  memset(M, 0, sizeof(*M));
+  bool used[3] = {false, false, false};
+  for (int i = 0; i < L.n_rects; ++i) used[stage_map(L.rects[i].log_tpr)] = true;
+  const int lays[3] = {2, 3, 5};
+  for (int m = 0; m < 3; ++m) {
+    if (!used[m]) continue;
+    const int lay = lays[m];
+    const int bw = stage_box_w(lay, T.rx, q), bh = sl_th(lay) + 2 * T.ry;
+    if (bw > 256 || bh > 256 || (size_t)bw * bh * es + 1024 > (size_t)kSlQ * kThreads * sizeof(float2)) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)L.nx, (cuuint64_t)L.ny};
+    const cuuint64_t strides[1] = {(cuuint64_t)L.nx * es};
+    const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&M->map[m], dt, 2, const_cast<void*>(L.elev), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
 }
 
 template <typename E, bool COMP>
 cudaError_t launch_typed(const Tables& T, const Launch& Lreq, cudaStream_t stream) {
   Launch L = Lreq;
-  if (!COMP) {
+  {
     decompose_sl(L);
     // 16-byte stores of whole cell blocks need 4 | nx (no ring wrap inside a block) and
     // aligned output planes
@@ -819,10 +1011,13 @@ cudaError_t launch_typed(const Tables& T, const Launch& Lreq, cudaStream_t strea
     const size_t smem = smem_sl(T, L);
     if (smem <= 227 * 1024) {
       if (L.tile_start[L.n_rects] == 0) return cudaSuccess;
-      auto kern = assess_kernel_sl<E>;
+      StageMaps M;
+      L.tma = stage_maps<E>(T, L, &M) ? 1 : 0;
+      if (!L.tma) memset(&M, 0, sizeof(M));
+      auto kern = assess_kernel_sl<E, COMP>;
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      return launch_pdl(kern, dim3(L.tile_start[L.n_rects], T.n_pairs), dim3(kThreads), smem, stream, T, L);
+      return launch_pdl(kern, dim3(L.tile_start[L.n_rects], T.n_pairs), dim3(kThreads), smem, stream, T, L, M);
     }
     // very large footprints: the per-cell kernel below
   }
@@ -855,9 +1050,36 @@ cudaError_t launch_assess(const Tables& T, const Launch& L, int elev_dtype, int 
     case SEB_BF16:
       return comp ? launch_typed<__nv_bfloat16, true>(T, L, stream)
                   : launch_typed<__nv_bfloat16, false>(T, L, stream);
+    case SEB_BF16_TILED:
+      return comp ? launch_typed<Bf16Tiled, true>(T, L, stream) : launch_typed<Bf16Tiled, false>(T, L, stream);
     default:
       return comp ? launch_typed<__half, true>(T, L, stream) : launch_typed<__half, false>(T, L, stream);
   }
+}
+
+// SEB_BF16_TILED encoding: one CTA per 16 x 16 world-aligned tile of the window.
+__global__ void encode_tiled_kernel(const float* __restrict__ elev, int nx, int ny, int px, int py, int tx_n,
+                                    __nv_bfloat16* __restrict__ delta, float* __restrict__ base) {
+  __shared__ float lo[256], hi[256];
+  seb::pdl_entry();
+  const int tx = blockIdx.x, ty = blockIdx.y, t = threadIdx.x;
+  const int c = tx * kBaseTile - px + (t & 15), r = ty * kBaseTile - py + (t >> 4);
+  const bool in = c >= 0 && c < nx && r >= 0 && r < ny;
+  const float z = in ? elev[(int64_t)r * nx + c] : __int_as_float(0x7fc00000);
+  const bool known = z == z;
+  lo[t] = known ? z : INFINITY;
+  hi[t] = known ? z : -INFINITY;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (t < s) {
+      lo[t] = fminf(lo[t], lo[t + s]);
+      hi[t] = fmaxf(hi[t], hi[t + s]);
+    }
+    __syncthreads();
+  }
+  const float b = lo[0] <= hi[0] ? 0.5f * lo[0] + 0.5f * hi[0] : 0.f;
+  if (t == 0) base[ty * tx_n + tx] = b;
+  if (in) delta[(int64_t)r * nx + c] = __float2bfloat16_rn(z - b);
 }
 
 cudaError_t launch_copy_out(const Launch& L, float* out_dev, uint8_t* flags_dev, cudaStream_t stream) {
@@ -869,3 +1091,28 @@ cudaError_t launch_copy_out(const Launch& L, float* out_dev, uint8_t* flags_dev,
 }
 
 }  // namespace seb
+
+extern "C" int seb_encode_bf16_tiled(const float* elev, int32_t nx, int32_t ny, int64_t oi, int64_t oj, void* out,
+                                     seb_stream_t stream) {
+  SEB_RANGE();
+  if (!elev || !out || nx < 1 || ny < 1 || ((uintptr_t)out & 255)) {
+    seb::set_error("seb_encode_bf16_tiled: NULL pointer, empty window or output not 256-byte aligned");
+    return SEB_ERR_INVALID_ARG;
+  }
+  if ((int64_t)nx * ny > (int64_t)1 << 31) {
+    seb::set_error("seb_encode_bf16_tiled: window too large");
+    return SEB_ERR_BAD_SHAPE;
+  }
+  const int px = (int)(((oi % seb::kBaseTile) + seb::kBaseTile) % seb::kBaseTile);
+  const int py = (int)(((oj % seb::kBaseTile) + seb::kBaseTile) % seb::kBaseTile);
+  const int txn = seb::tiled_tx(nx), tyn = seb::tiled_tx(ny);
+  auto* delta = static_cast<__nv_bfloat16*>(out);
+  auto* base = reinterpret_cast<float*>(static_cast<uint8_t*>(out) + seb::tiled_base_offset(nx, ny));
+  const cudaError_t e = seb::launch_pdl(seb::encode_tiled_kernel, dim3(txn, tyn), dim3(256), 0, (cudaStream_t)stream,
+                                        elev, (int)nx, (int)ny, px, py, txn, delta, base);
+  if (e != cudaSuccess) {
+    seb::set_error("seb_encode_bf16_tiled launch: %s", cudaGetErrorString(e));
+    return SEB_ERR_CUDA;
+  }
+  return SEB_OK;
+}

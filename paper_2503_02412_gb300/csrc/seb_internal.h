@@ -73,6 +73,11 @@ struct Launch {
   int32_t phase_x, phase_y;  // window origin mod 4 / mod 2 (global alignment of cell blocks)
   int32_t vec4;              // whole 4-cell blocks may be stored with 16-byte stores
   int32_t early;             // a later launch of a shift batch (seb_map_shift_batch): see the kernel
+  int32_t tma;               // stage the tile with one TMA copy per CTA (set by the launcher)
+  int32_t all_masked;        // every row run takes the masked moment path (rolling-shift bands)
+  // SEB_BF16_TILED windows: the FP32 bases [TY][TX] and the window's phase in the 16-cell tiles
+  const float* tile_base;
+  int32_t base_tx, base_px, base_py;
   int32_t n_rects;
   Rect rects[kMaxRects];
   int32_t tile_start[kMaxRects + 1];
@@ -95,7 +100,8 @@ struct Control {
 constexpr size_t kControlBytes = 256;
 
 enum DeviceError : uint32_t {
-  kErrLaunchShape = 1u,  // blockDim / grid disagree with the launch record
+  kErrLaunchShape = 1u,    // blockDim / grid disagree with the launch record
+  kErrStageTimeout = 2u,   // a CTA's bounded wait for its staged tile (TMA copy) ran out
 };
 
 // Continuous-pose query: the yaw-0 footprint lattice (a __grid_constant__ parameter).
@@ -121,6 +127,11 @@ struct QLaunch {
   float w0, w1, w2;
   float gap_fp64;
 };
+
+// SEB_BF16_TILED windows: 16 x 16 world-aligned tiles.
+constexpr int kBaseTile = 16;
+inline int tiled_tx(int nx) { return (nx + kBaseTile - 1) / kBaseTile + 1; }
+inline size_t tiled_base_offset(int nx, int ny) { return ((size_t)nx * ny * 2 + 255) & ~(size_t)255; }
 
 // Host helpers (seb_tables.cpp).  build_tables and build_lattice use no heap memory.
 int build_tables(const seb_params& p, Tables* T, int32_t* total_runs);

@@ -605,6 +605,10 @@ int query_setup(const seb_params& p, const void* elev, int64_t oi, int64_t oj, c
                 QTab* Q, QLaunch* L) {
   int rc = validate_params(p);
   if (rc) return rc;
+  if (p.elev_dtype == SEB_BF16_TILED) {
+    set_error("the continuous query reads FP32, BF16 or FP16 elevation, not SEB_BF16_TILED windows");
+    return SEB_ERR_INVALID_ARG;
+  }
   Tables T;  // on the stack: the allocation-free query shares this path
   rc = build_tables(p, &T, nullptr);
   if (rc) return rc;

@@ -24,7 +24,8 @@ int validate_params(const seb_params& p) {
   if (p.shape != SEB_RECT && p.shape != SEB_ELLIPSE) return SEB_ERR_INVALID_ARG;
   if (!(p.kappa_max > 0.f) || !(p.phi_x_max > 0.f) || !(p.phi_y_max > 0.f))
     return SEB_ERR_INVALID_ARG;
-  if (p.elev_dtype != SEB_F32 && p.elev_dtype != SEB_BF16 && p.elev_dtype != SEB_F16)
+  if (p.elev_dtype != SEB_F32 && p.elev_dtype != SEB_BF16 && p.elev_dtype != SEB_F16 &&
+      p.elev_dtype != SEB_BF16_TILED)
     return SEB_ERR_INVALID_ARG;
   if (p.precision != SEB_PLAIN_F32 && p.precision != SEB_COMPENSATED) return SEB_ERR_INVALID_ARG;
   if (p.n_min < 0) return SEB_ERR_INVALID_ARG;

@@ -8,7 +8,9 @@ import torch
 
 from . import abi
 
-DTYPES = {torch.float32: abi.SEB_F32, torch.bfloat16: abi.SEB_BF16, torch.float16: abi.SEB_F16}
+DTYPES = {torch.float32: abi.SEB_F32, torch.bfloat16: abi.SEB_BF16, torch.float16: abi.SEB_F16,
+          "bf16_tiled": abi.SEB_BF16_TILED}
+TILE = 16  # SEB_BF16_TILED: world-aligned tiles of 16 x 16 cells
 CHANNELS = ("z", "pitch", "roll", "rough", "risk")
 
 
@@ -88,6 +90,13 @@ class SebMap:
 
     def _check_elev(self, elev):
         p = self.params
+        if p.elev_dtype == "bf16_tiled":
+            n = abi.seb_window_bytes(self._p)
+            if elev.dtype != torch.uint8 or elev.numel() != n or not elev.is_cuda or not elev.is_contiguous():
+                raise ValueError(f"a bf16_tiled window is a contiguous CUDA uint8 tensor of {n} bytes "
+                                 "(encode_bf16_tiled / tiled_window)")
+            self._elev = elev
+            return
         if elev.dtype != p.elev_dtype or tuple(elev.shape) != (p.ny, p.nx) or not elev.is_cuda:
             raise ValueError(f"elevation must be a CUDA {p.elev_dtype} tensor of shape ({p.ny}, {p.nx})")
         if not elev.is_contiguous():
@@ -137,3 +146,37 @@ class SebMap:
     def check(self, timeout_ms=10000):
         abi.seb_map_set_stream(self.handle, _stream(self.device))
         return abi.seb_map_check(self.handle, timeout_ms)
+
+
+def encode_bf16_tiled(elev: torch.Tensor, origin=(0, 0)) -> torch.Tensor:
+    """FP32 elevation [ny][nx] on the device -> a SEB_BF16_TILED window buffer (uint8): BF16
+    offsets from an FP32 base per 16 x 16 world-aligned tile (seb_encode_bf16_tiled)."""
+    if elev.dtype != torch.float32 or elev.dim() != 2 or not elev.is_cuda or not elev.is_contiguous():
+        raise ValueError("elevation must be a contiguous CUDA float32 [ny][nx] tensor")
+    ny, nx = elev.shape
+    p = SebParams(nx=nx, ny=ny, elev_dtype="bf16_tiled").c()
+    out = torch.empty(abi.seb_window_bytes(p), dtype=torch.uint8, device=elev.device)
+    abi.seb_encode_bf16_tiled(elev.data_ptr(), nx, ny, int(origin[0]), int(origin[1]), out.data_ptr(),
+                              _stream(elev.device))
+    return out
+
+
+def tiled_parts(buf: torch.Tensor, nx: int, ny: int):
+    """Views of a SEB_BF16_TILED buffer: (offsets [ny][nx] bfloat16, bases [TY][TX] float32)."""
+    off = abi.seb_tiled_base_offset(nx, ny)
+    tx, ty = (nx + TILE - 1) // TILE + 1, (ny + TILE - 1) // TILE + 1
+    return (buf[:nx * ny * 2].view(torch.bfloat16).view(ny, nx),
+            buf[off:off + 4 * tx * ty].view(torch.float32).view(ty, tx))
+
+
+def tiled_window(world: torch.Tensor, world_nx: int, world_ny: int, oi: int, oj: int, nx: int, ny: int) -> torch.Tensor:
+    """Cuts the window at world cell (oi, oj) (0 <= oi, oi + nx <= world_nx, same for rows) of
+    size nx x ny out of a SEB_BF16_TILED encoding of a whole world made at origin (0, 0)."""
+    wd, wb = tiled_parts(world, world_nx, world_ny)
+    p = SebParams(nx=nx, ny=ny, elev_dtype="bf16_tiled").c()
+    out = torch.zeros(abi.seb_window_bytes(p), dtype=torch.uint8, device=world.device)
+    d, b = tiled_parts(out, nx, ny)
+    d.copy_(wd[oj:oj + ny, oi:oi + nx])
+    bt = wb[oj // TILE:oj // TILE + b.shape[0], oi // TILE:oi // TILE + b.shape[1]]
+    b[:bt.shape[0], :bt.shape[1]].copy_(bt)
+    return out

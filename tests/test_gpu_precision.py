@@ -101,3 +101,104 @@ def test_fp64_eigen_path(seb, terrain):
                                        with_gap=True)
     compare(out.cpu().numpy().reshape(5, -1).T, fl.reshape(-1), ref.reshape(5, -1).T, rfl.reshape(-1),
             label="fp64", gap=gap.reshape(-1))
+
+
+def _reconstruct_tiled(seb, buf, nx, ny, origin=(0, 0)):
+    """Heights a SEB_BF16_TILED window stands for: base of the cell's world tile + offset (FP32)."""
+    d, b = seb.tiled_parts(buf, nx, ny)
+    d = d.float().cpu().numpy()
+    b = b.cpu().numpy()
+    px, py = origin[0] % 16, origin[1] % 16
+    r = (np.arange(ny) + py) // 16
+    c = (np.arange(nx) + px) // 16
+    return (b[r][:, c] + d).astype(np.float32)
+
+
+def test_bf16_tiled_encoding(seb):
+    """The encoder: per 16 x 16 world tile, base = midpoint of the smallest and largest known
+    height, offsets = BF16 round-to-nearest of height - base, NaN kept; at a window origin that
+    is not a multiple of 16 the tiles follow the world grid."""
+    for origin in ((0, 0), (5, -13)):
+        e = bumpy_plane(3, 100, 72, 0.05)
+        e[10:14, 20:31] = np.nan
+        e[32:48, 48:64] = np.nan  # one whole world tile unknown at origin (0, 0)
+        buf = seb.encode_bf16_tiled(torch.from_numpy(e).cuda(), origin)
+        d, b = seb.tiled_parts(buf, 100, 72)
+        px, py = origin[0] % 16, origin[1] % 16
+        bw = np.zeros(b.shape, np.float32)
+        for ty in range(b.shape[0]):
+            for tx in range(b.shape[1]):
+                t = e[max(ty * 16 - py, 0):max(ty * 16 - py + 16, 0), max(tx * 16 - px, 0):max(tx * 16 - px + 16, 0)]
+                k = t[np.isfinite(t)]
+                bw[ty, tx] = np.float32(0.5) * k.min() + np.float32(0.5) * k.max() if k.size else 0.0
+        assert np.array_equal(b.cpu().numpy()[:bw.shape[0], :bw.shape[1]], bw)
+        r = (np.arange(72) + py) // 16
+        c = (np.arange(100) + px) // 16
+        want = (torch.from_numpy(e) - torch.from_numpy(bw[r][:, c])).to(torch.bfloat16)
+        got = d.cpu()
+        nan = torch.isnan(want)
+        assert torch.equal(torch.isnan(got), nan)  # NaN stays NaN (its payload is not fixed)
+        assert torch.equal(got[~nan].view(torch.int16), want[~nan].view(torch.int16))
+
+
+def test_bf16_tiled_parity_and_error(seb, terrain, record_property):
+    """SEB_BF16_TILED on the 1024 x 1024 map: parity against the oracle on the heights the
+    encoding stands for, and the storage error against the unquantised terrain, next to plain
+    BF16 (whose quantum at 8-16 m is 2^-4 m)."""
+    e, cells = terrain
+    buf = seb.encode_bf16_tiled(torch.from_numpy(e.astype(np.float32)).cuda())
+    g, f, _ = gpu_sample_tiled(seb, buf, cells)
+    eq = _reconstruct_tiled(seb, buf, 1024, 1024).astype(np.float64)
+    r, rf, gap = oracle.assess_cells(oracle.OracleParams(**C3), eq, cells)
+    compare(g, f, r, rf, label="bf16 tiled", gap=gap)
+    r0, rf0, _ = oracle.assess_cells(oracle.OracleParams(**C3), e, cells)
+    gb, fb, _ = gpu_sample(seb, torch.from_numpy(e).to("cuda", dtype=torch.bfloat16), cells)
+    ok = ((rf0 & 5) == 0) & ((f & 5) == 0) & ((fb & 5) == 0)
+    for ch, name in enumerate(("z", "pitch", "roll", "rough", "risk")):
+        dt = np.abs(g[ok, ch] - r0[ok, ch])
+        db = np.abs(gb[ok, ch] - r0[ok, ch])
+        record_property(f"bf16_tiled_{name}_max", float(dt.max()))
+        record_property(f"bf16_tiled_{name}_p99", float(np.percentile(dt, 99)))
+        print(f"{name}: tiled max {dt.max():.3g} p99 {np.percentile(dt, 99):.3g}; "
+              f"bf16 max {db.max():.3g} p99 {np.percentile(db, 99):.3g}")
+        if name in ("z", "pitch", "roll"):
+            assert np.percentile(dt, 99) < 0.25 * np.percentile(db, 99)
+    assert np.abs(g[ok, 1] - r0[ok, 1]).max() < 5e-3
+
+
+def gpu_sample_tiled(seb, buf, cells, **kw):
+    m = seb.SebMap(seb.SebParams(**C3, elev_dtype="bf16_tiled", **kw))
+    m.update(buf, (0, 0))
+    g = m.out_phys[:, cells[:, 2], cells[:, 1], cells[:, 0]].T.cpu().numpy()
+    f = m.flags_phys[cells[:, 2], cells[:, 1], cells[:, 0]].cpu().numpy()
+    return g, f, m.check()
+
+
+@pytest.mark.parametrize("form", ["compensated", "bf16_tiled"])
+def test_rolling_bit_identical_in_reduced_precision_forms(seb, form):
+    """The compensated sums and the tiled BF16 storage keep the rolling map bit-identical to a
+    rebuild: every cell's arithmetic depends on its neighbourhood only."""
+    from synthetic import fractal_world, shift_sequence
+
+    n, W = 160, 420
+    world = torch.from_numpy(fractal_world(8, W)).cuda()
+    kw = dict(nx=n, ny=n, n_yaw=72, res=0.05, length=0.9, width=0.6)
+    if form == "compensated":
+        p = seb.SebParams(**kw, precision="compensated")
+        win = lambda o: world[o[1]:o[1] + n, o[0]:o[0] + n].contiguous()  # noqa: E731
+    else:
+        p = seb.SebParams(**kw, elev_dtype="bf16_tiled")
+        enc = seb.encode_bf16_tiled(world)
+        win = lambda o: seb.tiled_window(enc, W, W, o[0], o[1], n, n)  # noqa: E731
+    o = [130, 130]
+    m = seb.SebMap(p)
+    m.update(win(o), tuple(o))
+    for dx, dy in shift_sequence(9, 14, 7):
+        o = [min(max(o[0] + dx, 0), W - n), min(max(o[1] + dy, 0), W - n)]
+        m.shift(win(o), tuple(o))
+    ro, rf = m.outputs()
+    full = seb.SebMap(p)
+    full.update(win(o), tuple(o))
+    fo, ff = full.outputs()
+    assert torch.equal(ro.view(torch.int32), fo.view(torch.int32)) and torch.equal(rf, ff)
+    m.check()

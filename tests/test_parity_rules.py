@@ -4,7 +4,7 @@ tolerances."""
 import numpy as np
 import pytest
 
-from .parity import C_GAP, GAP_MIN, U32, compare
+from .parity import C_GAP, U32, compare
 
 
 def rows(n=6):
@@ -32,9 +32,10 @@ def test_plain_cells_hold_the_plain_tolerance():
 def test_ill_cells_are_checked_against_the_gap_bound():
     ref, fl = rows()
     gap = np.full(len(ref), 0.3)
-    gap[3] = 1e-7  # bound C_GAP u / 1e-7
-    bound = C_GAP * U32 / 1e-7
-    assert bound > 1e-4 and 1e-7 < GAP_MIN
+    gap[3] = 1e-7  # bound C_GAP u / (1e-7 n_z)
+    nz = np.sqrt(1 - np.sin(0.1) ** 2 - np.sin(-0.05) ** 2)
+    bound = C_GAP * U32 / (1e-7 * nz)
+    assert bound > 1e-4
     gpu = ref.copy()
     gpu[3, 1] += 0.9 * bound
     s = compare(gpu, fl, ref, fl, gap=gap)
