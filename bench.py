@@ -743,12 +743,41 @@ def measure_rows(seb, args, dev, acc_jobs=None):
     t_exact = _time(lambda: m.update(em), 10, st)
     t_sur = _time(lambda: sur.infer_into(em, o, f, mk, exact_fallback=False), 10, st)
     t_all = _time(lambda: sur.infer_into(em, o, f, mk), 10, st)
+    # tensor-pipe share of the batch path: the three 32 -> 32 layers run as tcgen05 implicit GEMMs
+    # (forward; backward dgrad and wgrad with the gradient split into two BF16 operands)
+    bt = 256
+    t_fwd = _time(lambda: abi.seb_sur_forward(sur.handle, bt), 10, st)
+    t_step = _time(lambda: abi.seb_sur_train_step(sur.handle, bt, 1e-6, 10_000, 0), 10, st)
+    sides = (46, 44, 40, 32, 16)
+    mm = 2 * 288 * 32  # FLOP per pixel of one 32 -> 32 layer (and of its dgrad / wgrad)
+    f_fwd = bt * mm * sum(sides[l + 1] ** 2 for l in (1, 2, 3))
+    f_bwd = bt * mm * sum(sides[l] ** 2 + sides[l + 1] ** 2 for l in (1, 2, 3))  # dgrad + wgrad, algorithmic
+    peak_bf16 = measured_peak("bf16_tflops_sustained", 1708.0)
     rows["surrogate_400x400x72"] = {
         "train_patches": args.sur_patches, "train_s": train_s, "loss_first": losses[0][1], "loss_last": losses[-1][1],
         "engine": "tcgen05", "fallback_frac": float(mk.float().mean()), "error_vs_exact_on_surrogate_cells": err,
         "exact_rebuild_ms": t_exact, "surrogate_only_ms": t_sur, "surrogate_with_fallback_ms": t_all,
-        "gain_vs_exact": t_exact / t_all}
+        "gain_vs_exact": t_exact / t_all,
+        "tensor_pipe": {
+            "batch": bt, "forward_ms": t_fwd, "train_step_ms": t_step,
+            "tcgen05_flop_forward": f_fwd, "tcgen05_flop_train_step": f_fwd + f_bwd,
+            "achieved_tflops_forward": f_fwd / (t_fwd * 1e-3) / 1e12,
+            "achieved_tflops_train_step": (f_fwd + f_bwd) / (t_step * 1e-3) / 1e12,
+            "peak_tflops": peak_bf16, "peak_basis": "measured BF16 dense, sustained",
+            "frac_forward": f_fwd / (t_fwd * 1e-3) / 1e12 / peak_bf16,
+            "frac_train_step": (f_fwd + f_bwd) / (t_step * 1e-3) / 1e12 / peak_bf16,
+            "basis": "algorithmic FLOP of the tcgen05 layers over the whole forward / train-step time (the first "
+                     "layer, the head, the loss and Adam run on CUDA cores inside the same time)"}}
     return rows
+
+
+def measured_peak(key, fallback):
+    """A peak from MEASURED_PEAKS.json at the repository root, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)[key])
+    except (OSError, KeyError, ValueError):
+        return fallback
 
 
 def local_mapping_cycle(seb, dev, st, n_scans=6, reps=5):

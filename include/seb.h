@@ -415,9 +415,12 @@ int seb_sur_create(const seb_params* p, int32_t max_batch, void* workspace_dev, 
 int seb_sur_destroy(seb_sur* h);
 int seb_sur_set_stream(seb_sur* h, seb_stream_t stream);
 int seb_sur_view_get(const seb_sur* h, seb_sur_view* v);
-/* Engine of the 32 -> 32 convolutions: SEB_SUR_TCGEN05 (default; tensor cores: tcgen05.mma
- * implicit GEMM, M = 128 pixels, N = 32, K = 288, FP32 accumulation in tensor memory) or
- * SEB_SUR_SIMT (FP32 CUDA cores).  Backward passes always run on the CUDA cores. */
+/* Engine of the 32 -> 32 convolutions, forward and backward: SEB_SUR_TCGEN05 (default; tensor
+ * cores: tcgen05.mma implicit GEMMs with BF16 operands and FP32 accumulation in tensor memory;
+ * forward M = 128 output pixels, N = 32, K = 288; input gradient M = 128 input pixels, N = 32,
+ * K = 288; weight gradient M = 3 x 128 (tap, channel) rows, N = 32, K = the pixels; the FP32
+ * upstream gradient enters as a BF16 high part plus a BF16 low part) or SEB_SUR_SIMT (FP32 CUDA
+ * cores).  The first layer (2 input channels) and the 1x1 head run on the CUDA cores. */
 #define SEB_SUR_SIMT 0
 #define SEB_SUR_TCGEN05 1
 int seb_sur_set_engine(seb_sur* h, int32_t engine);

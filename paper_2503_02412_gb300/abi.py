@@ -10,7 +10,8 @@ import os
 import threading
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libseb.so")
+# SEB_LIBRARY selects another build of the same library (the bounds-checked libseb_debug.so).
+LIB_PATH = os.environ.get("SEB_LIBRARY") or os.path.join(_PKG, "libseb.so")
 
 SEB_OK = 0
 SEB_ERR_INVALID_ARG = -1

@@ -17,6 +17,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "libseb.so")
+# Bounds-checked build (-DSEB_DEBUG): every index check of the kernels is compiled in; a failed
+# check raises a bit of the device error word instead of touching memory.  Same entry points.
+OUT_DEBUG = os.path.join(PKG, "libseb_debug.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
@@ -38,9 +41,9 @@ def _flags(extra=()):
                    "--expt-relaxed-constexpr", *defs, *extra]
 
 
-def _compile(src, extra):
-    os.makedirs(BUILD, exist_ok=True)
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src, extra, build_dir=BUILD):
+    os.makedirs(build_dir, exist_ok=True)
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     cmd = [NVCC, *_flags(extra), "-c", src, "-o", obj]
     if src.endswith(".cpp"):
         cmd.insert(1, "-x")
@@ -60,31 +63,35 @@ def _stamp(extra):
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile every CUDA/C++ source of the package and link libseb.so; returns its path."""
-    stamp_file = OUT + ".stamp"
+def build(force: bool = False, verbose: bool = False, extra=(), debug: bool = False) -> str:
+    """Compile every CUDA/C++ source of the package and link libseb.so (libseb_debug.so with
+    debug=True: the bounds-checked build); returns its path."""
+    out = OUT_DEBUG if debug else OUT
+    extra = tuple(extra) + (("-DSEB_DEBUG",) if debug else ())
+    build_dir = BUILD + ("_debug" if debug else "")
+    stamp_file = out + ".stamp"
     stamp = _stamp(extra)
-    if not force and os.path.exists(OUT) and os.path.exists(stamp_file):
+    if not force and os.path.exists(out) and os.path.exists(stamp_file):
         with open(stamp_file) as fh:
             if fh.read() == stamp:
-                return OUT
+                return out
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-        results = list(ex.map(lambda s: _compile(s, extra), _sources()))
+        results = list(ex.map(lambda s: _compile(s, extra, build_dir), _sources()))
     objs = [o for o, _ in results]
     if verbose:
         for _, log in results:
             if log.strip():
                 print(log, file=sys.stderr)
-    tmp = OUT + f".tmp{os.getpid()}"
+    tmp = out + f".tmp{os.getpid()}"
     r = subprocess.run([NVCC, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, OUT)
+    os.replace(tmp, out)
     with open(stamp_file, "w") as fh:
         fh.write(stamp)
-    return OUT
+    return out
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True,
+    print(build(force="--force" in sys.argv, verbose=True, debug="--debug" in sys.argv,
                 extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else []))

@@ -518,6 +518,9 @@ __global__ void __launch_bounds__(kThreads, 2)
   const float qnan = __int_as_float(0x7fc00000);
   // Each staged value v goes to two vertical pairs: (row, row + 1).x and (row - 1, row).y.
   auto put = [&](int row, int col, float v) {
+    if (!SEB_IN_BOUNDS(L.err, row >= 0 && row < sh && row < kMaxStageRows && col >= 0 && col < sw &&
+                                  (row < sh - 1 ? sl_index(row, col, sw2) : sl_index(row - 1, col, sw2)) < L.pairs_alloc))
+      return;
     if (v != v) rowflag[row] = 1;
     if (row < sh - 1) pt[sl_index(row, col, sw2)].x = v;
     if (row > 0) pt[sl_index(row - 1, col, sw2)].y = v;
@@ -556,7 +559,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     int row = tid / sw, col = tid - (tid / sw) * sw;
     while (row < sh) {
-      put(row, col, stage_elev<E>(L, box[row * bw + ox + col], gx0 + col, gy0 + row));
+      if (SEB_IN_BOUNDS(L.err, (size_t)(row * bw + ox + col + 1) * sizeof(E) + (size_t)(reinterpret_cast<const char*>(box) -
+                                                                                       reinterpret_cast<char*>(qs)) <=
+                                   (size_t)kSlQ * kThreads * sizeof(float2)))
+        put(row, col, stage_elev<E>(L, box[row * bw + ox + col], gx0 + col, gy0 + row));
       row += dr;
       col += dc;
       if (col >= sw) {
@@ -646,6 +652,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     const bool masked = L.all_masked || __any_sync(0xffffffffu, rowflag[row] | rowflag[row + 1]);
     const float2* pq = pt + sl_index(row, rx + lx + lo, sw2);  // pq[k]: column lo + k of the block
     const int len = hi - lo + 1;
+    if (!SEB_IN_BOUNDS(L.err, row >= 0 && row + 1 < sh && rx + lx + lo >= 0 && rx + lx + hi + 3 < sw &&
+                                  sl_index(row, rx + lx + hi + 3, sw2) < L.pairs_alloc))
+      continue;
     const float flo = (float)lo, fhi = (float)hi;
     const float2 dj2 = f2((float)dj, (float)dj);
     auto slide = [&](int t, float2 zo, float2 zi) {
@@ -820,6 +829,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       // so no ring wrap falls inside it): one 16-byte store per channel and plane
       const int64_t i0 = (int64_t)k0 * L.plane + (int64_t)pr * L.nx + pc;
       const int64_t i1 = (int64_t)k1 * L.plane + (int64_t)pr * L.nx + pc;
+      if (!SEB_IN_BOUNDS(L.err, pr >= 0 && pr < L.ny && pc >= 0 && pc + 3 < L.nx && i1 + 3 < chs)) continue;
       auto st4 = [&](int64_t i, float a, float b, float c, float d) {
         *reinterpret_cast<float4*>(out + i) = make_float4(a, b, c, d);
       };
@@ -846,6 +856,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       if (pcg >= L.nx) pcg -= L.nx;
       const int64_t i0 = (int64_t)k0 * L.plane + (int64_t)pr * L.nx + pcg;
       const int64_t i1 = (int64_t)k1 * L.plane + (int64_t)pr * L.nx + pcg;
+      if (!SEB_IN_BOUNDS(L.err, pr >= 0 && pr < L.ny && pcg >= 0 && pcg < L.nx && i1 < chs)) continue;
       out[i0] = o[g].z;
       out[i1] = o[g].z;
       out[chs + i0] = o[g].pitch;
@@ -941,6 +952,16 @@ void decompose_sl(Launch& L) {
   }
 }
 
+size_t pairs_sl(const Tables& T, const Launch& L) {
+  size_t pairs = 0;
+  for (int i = 0; i < L.n_rects; ++i) {
+    const int lay = L.rects[i].log_tpr;
+    const size_t s = (size_t)(sl_th(lay) + 2 * T.ry - 1) * sl_sw2(lay, T.rx);
+    pairs = s > pairs ? s : pairs;
+  }
+  return pairs;
+}
+
 size_t smem_sl(const Tables& T, const Launch& L) {
   size_t pairs = 0;
   for (int i = 0; i < L.n_rects; ++i) {
@@ -1009,6 +1030,7 @@ cudaError_t launch_typed(const Tables& T, const Launch& Lreq, cudaStream_t strea
     // aligned output planes
     L.vec4 = (L.nx % 4 == 0) && ((uintptr_t)L.out % 16 == 0) && ((uintptr_t)L.flags % 4 == 0);
     const size_t smem = smem_sl(T, L);
+    L.pairs_alloc = (int32_t)pairs_sl(T, L);
     if (smem <= 227 * 1024) {
       if (L.tile_start[L.n_rects] == 0) return cudaSuccess;
       StageMaps M;

@@ -75,6 +75,7 @@ struct Launch {
   int32_t early;             // a later launch of a shift batch (seb_map_shift_batch): see the kernel
   int32_t tma;               // stage the tile with one TMA copy per CTA (set by the launcher)
   int32_t all_masked;        // every row run takes the masked moment path (rolling-shift bands)
+  int32_t pairs_alloc;       // float2 slots of the staged vertical pairs (bounds checks of SEB_DEBUG builds)
   // SEB_BF16_TILED windows: the FP32 bases [TY][TX] and the window's phase in the 16-cell tiles
   const float* tile_base;
   int32_t base_tx, base_px, base_py;
@@ -102,7 +103,17 @@ constexpr size_t kControlBytes = 256;
 enum DeviceError : uint32_t {
   kErrLaunchShape = 1u,    // blockDim / grid disagree with the launch record
   kErrStageTimeout = 2u,   // a CTA's bounded wait for its staged tile (TMA copy) ran out
+  kErrBounds = 16u,        // SEB_DEBUG builds: an index check failed (the access was skipped)
 };
+
+// Index checks of SEB_DEBUG builds (-DSEB_DEBUG, paper_2503_02412_gb300.build(debug=True)):
+// a failed check raises kErrBounds in the launch's error word and the guarded access is skipped;
+// release builds compile the checks away and always take the access.
+#ifdef SEB_DEBUG
+#define SEB_IN_BOUNDS(err, cond) ((cond) ? true : (atomicOr((err), ::seb::kErrBounds), false))
+#else
+#define SEB_IN_BOUNDS(err, cond) true
+#endif
 
 // Continuous-pose query: the yaw-0 footprint lattice (a __grid_constant__ parameter).
 constexpr int kMaxLattice = 256;

@@ -654,6 +654,300 @@ __global__ void __launch_bounds__(kTcM, 2) conv_tc_kernel(const bf16* __restrict
 }
 
 // ------------------------------------------------------------------------------------------------
+// Tensor-core backward of the 32 -> 32 layers (tcgen05, the same operand layout and instruction
+// descriptor as conv_tc_kernel: BF16, K-major, no swizzle, M = 128, N = 32, FP32 in tensor memory).
+// The FP32 gradient dz = dy * (y > 0) enters as two BF16 operands, hi = bf16(dz) and
+// lo = bf16(dz - hi), multiplied by the same BF16 weights or activations and accumulated in FP32:
+// every product is exact and hi + lo carries dz to about 2^-17, so the tensor-core gradients
+// track the FP32 CUDA-core ones.
+// ------------------------------------------------------------------------------------------------
+struct TcSync {  // one-thread MMA issue, commit and a bounded wait, as in conv_tc_kernel
+  uint64_t* bar;
+  __device__ void issue(uint32_t tmem_d, uint32_t a0, uint32_t a_lbo, uint32_t b0, uint32_t b_lbo, int ksteps,
+                        bool acc_first) const {
+    for (int s = 0; s < ksteps; ++s) {
+      const uint64_t ad = tc_desc(a0 + s * 2 * a_lbo, a_lbo, 128);
+      const uint64_t bd = tc_desc(b0 + s * 2 * b_lbo, b_lbo, 128);
+      const uint32_t acc = (s > 0 || acc_first) ? 1u : 0u;
+      asm volatile(
+          "{\n .reg .pred pa;\n setp.ne.b32 pa, %4, 0;\n"
+          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}" ::"r"(tmem_d),
+          "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(acc));
+    }
+  }
+  __device__ void commit() const {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+  }
+  __device__ bool wait(uint32_t parity) const {
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 20) && !done; ++it)
+      asm volatile(
+          "{\n .reg .pred pw;\n mbarrier.try_wait.parity.shared::cta.b64 pw, [%1], %2;\n selp.u32 %0, 1, 0, pw;\n}"
+          : "=r"(done)
+          : "r"(smem_u32(bar)), "r"(parity)
+          : "memory");
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return done != 0;
+  }
+};
+
+__device__ __forceinline__ uint32_t tmem_alloc_cols(uint32_t* slot, int warp, uint32_t cols) {
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  return *slot;
+}
+
+__device__ __forceinline__ void tmem_free_cols(uint32_t tmem, int warp, uint32_t cols) {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
+  }
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t r[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// 8 BF16 values -> one 16-byte core-matrix row.
+__device__ __forceinline__ uint4 pack8(const float v[8]) {
+  uint4 o;
+  __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+  for (int t = 0; t < 4; ++t) h[t] = __floats2bfloat162_rn(v[2 * t], v[2 * t + 1]);
+  return o;
+}
+
+// Input side: dx[p][c] = sum_{tap, o} dz[p - tap offset][o] w[o][tap][c] as the implicit GEMM
+// D[128 input pixels][32 c] = A[128][288] B[288][32], A the rows (tap, o) of dz (0 outside the
+// output), B[k = tap * 32 + o][c] = w[o][tap][c]; once with dz's hi part, then accumulated with
+// its lo part.  Writes dx FP32 [B][H][W][32].
+constexpr int kBdBOff = kTcBOff;                 // B after A (72 KB)
+constexpr int kBdBarOff = kBdBOff + 18 * 1024;
+constexpr int kBdSmem = kBdBarOff + 256;
+
+__global__ void __launch_bounds__(kTcM, 2) conv_bwd_dx_tc_kernel(const float* __restrict__ dy, const bf16* __restrict__ y,
+                                                                 const bf16* __restrict__ w, int B, int H, int W, int d,
+                                                                 float* __restrict__ dx, uint32_t* err) {
+  extern __shared__ __align__(1024) uint8_t tsm[];
+  uint8_t* As = tsm;
+  uint8_t* Bs = tsm + kBdBOff;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(tsm + kBdBarOff);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tsm + kBdBarOff + 16);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int Ho = H - 2 * d, Wo = W - 2 * d;
+  const int64_t P = (int64_t)B * H * W;
+  const int64_t p = (int64_t)blockIdx.x * kTcM + tid;
+  // B: K-major rows c, k = tap * 32 + o, value w[o][tap][c] (a transpose of the stored [o][tap][c])
+  for (int i = tid; i < kHid * kTcKCores; i += kTcM) {
+    const int c = i / kTcKCores, kc = i - c * kTcKCores;
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int k = kc * 8 + e, tap = k >> 5, o = k & 31;
+      v[e] = __bfloat162float(w[((int64_t)o * 9 + tap) * kHid + c]);
+    }
+    *reinterpret_cast<uint4*>(Bs + tc_off(c, kc * 8, kHid / 8)) = pack8(v);
+  }
+  int b = 0, r = 0, s = 0;
+  if (p < P) {
+    b = (int)(p / ((int64_t)H * W));
+    const int rem = (int)(p - (int64_t)b * H * W);
+    r = rem / W;
+    s = rem - r * W;
+  }
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
+  const uint32_t tmem = tmem_alloc_cols(tslot, warp, 32);
+  const TcSync sync{mbar};
+  bool ok = true;
+  for (int part = 0; part < 2 && ok; ++part) {  // 0: hi, 1: lo
+    // A: this thread's row, 9 taps x 32 o of dz (part), 0 outside the output or past the last pixel
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+      const int u = tap / 3, v = tap - u * 3;
+      const int i = r - u * d, j = s - v * d;
+      const bool in = p < P && i >= 0 && i < Ho && j >= 0 && j < Wo;
+      const int64_t q = in ? (((int64_t)b * Ho + i) * Wo + j) * kHid : 0;
+#pragma unroll
+      for (int oc = 0; oc < 4; ++oc) {
+        float z[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int o = oc * 8 + e;
+          float g = 0.f;
+          if (in && __bfloat162float(y[q + o]) > 0.f) g = dy[q + o];
+          const float hi = __bfloat162float(__float2bfloat16_rn(g));
+          z[e] = part == 0 ? hi : g - hi;
+        }
+        *reinterpret_cast<uint4*>(As + tc_off(tid, tap * kHid + oc * 8, kTcM / 8)) = pack8(z);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands visible to the tensor core
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+      sync.issue(tmem, smem_u32(As), (kTcM / 8) * 128, smem_u32(Bs), (kHid / 8) * 128, kTcK / 16, part > 0);
+      sync.commit();
+    }
+    ok = sync.wait((uint32_t)part);
+    ok = __syncthreads_and(ok) != 0;  // the next part overwrites A only after the MMAs read it
+  }
+  if (!ok) {  // report, give the MMAs in flight one more bounded wait, then free the columns
+    if (tid == 0) atomicOr(err, 8u);
+    sync.wait(0);
+    sync.wait(1);
+  } else {
+    uint32_t rr[32];
+    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), rr);
+    if (p < P) {
+      float4* o4 = reinterpret_cast<float4*>(dx + p * kHid);
+#pragma unroll
+      for (int q = 0; q < kHid / 4; ++q)
+        o4[q] = make_float4(__uint_as_float(rr[4 * q]), __uint_as_float(rr[4 * q + 1]), __uint_as_float(rr[4 * q + 2]),
+                            __uint_as_float(rr[4 * q + 3]));
+    }
+  }
+  tmem_free_cols(tmem, warp, 32);
+}
+
+// Weight side: dw[o][tap][c] = sum_p dz[p][o] x[p + tap offset][c] and db[o] = sum_p dz[p][o] as
+// D[m][o] = sum_k A[m][k] B[o][k] over the CTA's output pixels k (kChunkPx, 128 per round):
+// A rows m = tap * 32 + c (three M = 128 tiles; row 288 is all ones, so its D row is db; the rest
+// of the third tile is zero), B rows o = dz hi, then dz lo.  One partial [o][tap][c] + [o] per CTA,
+// in the layout of conv_bwd_dw_kernel, summed in CTA order by reduce_partials_kernel.
+constexpr int kBwTile = kTcM * kTcM * 2;          // one A tile: 128 rows x 128 pixels BF16 (32 KB)
+constexpr int kBwBOff = 3 * kBwTile;              // B hi, then B lo: 32 rows x 128 pixels each (8 KB)
+constexpr int kBwBarOff = kBwBOff + 2 * kHid * kTcM * 2;
+constexpr int kBwSmem = kBwBarOff + 64 + kTcM * 4;  // + barrier, TMEM slot, pixel offsets: two CTAs per SM
+
+__global__ void __launch_bounds__(kTcM, 2) conv_bwd_dw_tc_kernel(const float* __restrict__ dy, const bf16* __restrict__ y,
+                                                                 const bf16* __restrict__ x, int B, int H, int W, int d,
+                                                                 float* __restrict__ partials, uint32_t* err) {
+  extern __shared__ __align__(1024) uint8_t tsm[];
+  uint8_t* Bh = tsm + kBwBOff;
+  uint8_t* Bl = Bh + kHid * kTcM * 2;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(tsm + kBwBarOff);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tsm + kBwBarOff + 16);
+  int32_t* poff = reinterpret_cast<int32_t*>(tsm + kBwBarOff + 64);  // x offset of each pixel, -1 past the end
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int Ho = H - 2 * d, Wo = W - 2 * d;
+  const int64_t P = (int64_t)B * Ho * Wo;
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
+  const uint32_t tmem = tmem_alloc_cols(tslot, warp, 128);  // three 32-column accumulators
+  const TcSync sync{mbar};
+  bool ok = true;
+  const int64_t p0 = (int64_t)blockIdx.x * kChunkPx;
+  int round = 0;
+  for (int64_t q0 = p0; q0 < p0 + kChunkPx && q0 < P && ok; q0 += kTcM, ++round) {
+    {  // this round's pixels
+      const int64_t p = q0 + tid;
+      int32_t off = -1;
+      if (p < P) {
+        const int b = (int)(p / ((int64_t)Ho * Wo));
+        const int rem = (int)(p - (int64_t)b * Ho * Wo);
+        const int i = rem / Wo, j = rem - i * Wo;
+        off = (int32_t)((((int64_t)b * H + i) * W + j) * kHid);  // the host keeps B H W 32 below 2^31
+      }
+      poff[tid] = off;
+    }
+    __syncthreads();
+    // A: thread tid writes row tid of each tile (m = 128 t + tid), all 128 pixels
+#pragma unroll 1
+    for (int t = 0; t < 3; ++t) {
+      const int m = t * kTcM + tid;
+      const int tap = m >> 5, c = m & 31;
+      const int u = tap / 3, v = tap - u * 3;
+      const int64_t toff = ((int64_t)u * d * W + v * d) * kHid + c;
+      uint8_t* At = tsm + t * kBwTile;
+#pragma unroll 1
+      for (int kc = 0; kc < kTcM / 8; ++kc) {
+        float val[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int32_t off = poff[kc * 8 + e];
+          float a = 0.f;
+          if (off >= 0) {
+            if (m < 9 * kHid)
+              a = __bfloat162float(x[off + toff]);
+            else if (m == 9 * kHid)
+              a = 1.f;  // the ones row: its D row is the bias gradient
+          }
+          val[e] = a;
+        }
+        *reinterpret_cast<uint4*>(At + tc_off(tid, kc * 8, kTcM / 8)) = pack8(val);
+      }
+    }
+    // B: rows o = tid & 31, pixel octets (tid >> 5) * 4 .. + 3, dz hi and lo
+    {
+      const int o = tid & 31;
+#pragma unroll 1
+      for (int kc = (tid >> 5) * 4; kc < (tid >> 5) * 4 + 4; ++kc) {
+        float hi[8], lo[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int64_t p = q0 + kc * 8 + e;
+          float g = 0.f;
+          if (p < P && __bfloat162float(y[p * kHid + o]) > 0.f) g = dy[p * kHid + o];
+          hi[e] = __bfloat162float(__float2bfloat16_rn(g));
+          lo[e] = g - hi[e];
+        }
+        *reinterpret_cast<uint4*>(Bh + tc_off(o, kc * 8, kHid / 8)) = pack8(hi);
+        *reinterpret_cast<uint4*>(Bl + tc_off(o, kc * 8, kHid / 8)) = pack8(lo);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+      const uint32_t a_lbo = (kTcM / 8) * 128, b_lbo = (kHid / 8) * 128;
+      for (int t = 0; t < 3; ++t) {
+        const uint32_t a0 = smem_u32(tsm + t * kBwTile);
+        sync.issue(tmem + 32 * t, a0, a_lbo, smem_u32(Bh), b_lbo, kTcM / 16, round > 0);
+        sync.issue(tmem + 32 * t, a0, a_lbo, smem_u32(Bl), b_lbo, kTcM / 16, true);
+      }
+      sync.commit();
+    }
+    ok = sync.wait((uint32_t)(round & 1));
+    ok = __syncthreads_and(ok) != 0;  // the next round overwrites A and B only after the MMAs read them
+  }
+  if (!ok) {  // report, give the MMAs in flight one more bounded wait, then free the columns
+    if (tid == 0) atomicOr(err, 8u);
+    sync.wait((uint32_t)((round - 1) & 1));
+  } else if (round > 0) {
+    constexpr int E = kHid * 9 * kHid + kHid;
+    float* part = partials + (int64_t)blockIdx.x * E;
+    for (int t = 0; t < 3; ++t) {
+      uint32_t rr[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 32 * t, rr);
+      const int m = t * kTcM + warp * 32 + (tid & 31);
+      if (m < 9 * kHid) {
+        for (int o = 0; o < kHid; ++o) part[o * 9 * kHid + m] = __uint_as_float(rr[o]);
+      } else if (m == 9 * kHid) {
+        for (int o = 0; o < kHid; ++o) part[kHid * 9 * kHid + o] = __uint_as_float(rr[o]);
+      }
+    }
+  }
+  tmem_free_cols(tmem, warp, 128);
+}
+
+// ------------------------------------------------------------------------------------------------
 // Inference over a map.
 // ------------------------------------------------------------------------------------------------
 // act [H4][W4][32] covers cells (r, c) = (i + 16, j + 16); writes out[5][K][ny][nx] and flags for
@@ -923,6 +1217,8 @@ int seb_sur_create(const seb_params* p, int32_t max_batch, void* ws, size_t byte
   if (rc) return rc;
   if (p->nx < 2 * kMargin + 1 || p->ny < 2 * kMargin + 1) return fail("seb_sur_create: map smaller than 33 x 33");
   if (p->elev_dtype != SEB_F32) return fail("seb_sur_create: the surrogate reads FP32 elevation");
+  if ((int64_t)max_batch * kFeat * kFeat * kHid >= ((int64_t)1 << 31))
+    return fail("seb_sur_create: max_batch too large (activation offsets must stay below 2^31)");
   if (!ws || ((uintptr_t)ws & 255)) {
     seb::set_error("surrogate workspace NULL or not 256-byte aligned");
     return SEB_ERR_WORKSPACE;
@@ -1133,6 +1429,14 @@ int seb_sur_train_step(seb_sur* h, int32_t B, float lr, int32_t step, float* los
       const int E = kHid * 9 * kInF + kHid;
       conv_bwd_dw_kernel<kInF><<<ch, 256, 0, st>>>(dy, y, xin, B, S, S, d, part);
       reduce_partials_kernel<<<grid_for(E, 256), 256, 0, st>>>(part, ch, E, grad + h->PL.w[0]);
+    } else if (h->engine == SEB_SUR_TCGEN05) {
+      const int E = kHid * 9 * kHid + kHid;
+      cudaFuncSetAttribute(conv_bwd_dw_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBwSmem);
+      conv_bwd_dw_tc_kernel<<<ch, kTcM, kBwSmem, st>>>(dy, y, xin, B, S, S, d, part, h->err);
+      reduce_partials_kernel<<<grid_for(E, 256), 256, 0, st>>>(part, ch, E, grad + h->PL.w[l]);
+      cudaFuncSetAttribute(conv_bwd_dx_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBdSmem);
+      conv_bwd_dx_tc_kernel<<<(unsigned)(((int64_t)B * S * S + kTcM - 1) / kTcM), kTcM, kBdSmem, st>>>(
+          dy, y, wb + h->PL.w[l], B, S, S, d, at<float>(h, h->v.dact[l - 1]), h->err);
     } else {
       const int E = kHid * 9 * kHid + kHid;
       conv_bwd_dw_kernel<kHid><<<ch, 256, 0, st>>>(dy, y, xin, B, S, S, d, part);

@@ -235,7 +235,24 @@ def test_training_gain_report(mods, record_property):
     for k, v in res.items():
         record_property(k, v)
     print(res)
-    assert res["bumpy_pitch_p50"] < 0.05 and res["bumpy_roll_p50"] < 0.05
+    # Stated bounds on the cells the network predicts after this short run (40,960 patches; the
+    # exact kernel's own bar is 1e-4: the surrogate trades three orders of accuracy for its
+    # speed).  The bumpy plane is the training distribution; the fractal map (steps, unknown
+    # discs) lies outside it, so its bounds are wider.
+    bounds = {"bumpy": (0.05, 0.2, 0.2, 0.05), "fractal": (0.1, 0.4, 0.25, 0.06)}  # p50 angle, p99 angle, risk, z
+    for name, (a50, a99, k99, z99) in bounds.items():
+        assert res[f"{name}_pitch_p50"] < a50 and res[f"{name}_roll_p50"] < a50, name
+        assert res[f"{name}_pitch_p99"] < a99 and res[f"{name}_roll_p99"] < a99, name
+        assert res[f"{name}_risk_p99"] < k99 and res[f"{name}_z_p99"] < z99, name
+    # What the network gains: exact rebuild time over surrogate + exact fallback time.  On these
+    # maps the fallback cells (next to unknown cells, steps and the border) alone cost about a
+    # rebuild, so the gain is below 1 (a loss); it is reported, not assumed.
+    for name in ("bumpy", "fractal"):
+        gain = res[f"{name}_exact_ms"] / res[f"{name}_surrogate_ms"]
+        record_property(f"{name}_gain", gain)
+        print(f"{name}: surrogate + fallback {res[f'{name}_surrogate_ms']:.3f} ms, exact {res[f'{name}_exact_ms']:.3f} ms, "
+              f"gain {gain:.2f}, fallback {res[f'{name}_fallback_frac']:.2f} of the cells")
+        assert 0.2 < gain < 5.0
 
 
 @pytest.mark.parametrize("engine", ["tcgen05", "simt"])
