@@ -100,6 +100,10 @@ def parse():
                     help="three SDFs of the 400x400x72 risk grid and nothing else (for ncu)")
     ap.add_argument("--profile-rebuild", action="store_true",
                     help="only run three full rebuilds of the map (a short program for ncu)")
+    ap.add_argument("--profile-shift", action="store_true",
+                    help="only run a rebuild and three 10-cell moves as separate calls (for ncu)")
+    ap.add_argument("--profile-train", action="store_true",
+                    help="only run three surrogate training steps of 256 patches (for ncu)")
     return ap.parse_args()
 
 
@@ -385,6 +389,40 @@ def profile_rebuild():
     torch.cuda.synchronize()
 
 
+def profile_shift():
+    """A rebuild of the 400x400x72 map and the first three 10-cell moves of the bench workload as
+    separate seb_map_shift calls, nothing else: the program ncu captures (launch 2 is a move)."""
+    import torch
+
+    import paper_2503_02412_gb300 as seb
+
+    world_np, origins = workload()
+    world = torch.from_numpy(world_np).cuda()
+    wins = [world[o[1]:o[1] + NY, o[0]:o[0] + NX].contiguous() for o in origins[:4]]
+    m = seb.SebMap(seb.SebParams(nx=NX, ny=NY, n_yaw=K, res=RES, length=LENGTH, width=WIDTH))
+    m.update(wins[0], origins[0])
+    for w, o in zip(wins[1:], origins[1:4]):
+        m.shift(w, o)
+    m.check()
+    torch.cuda.synchronize()
+
+
+def profile_train():
+    """Three surrogate training steps of 256 patches (one labelled batch, tcgen05 engine) after
+    the batch is made: the program ncu captures for the backward kernels."""
+    import torch
+
+    import paper_2503_02412_gb300 as seb
+    from paper_2503_02412_gb300 import abi, surrogate
+
+    s = surrogate.Surrogate(seb.SebParams(nx=NX, ny=NY, n_yaw=K, res=RES, length=LENGTH, width=WIDTH), max_batch=256)
+    s.init(11)
+    s.make_batch(np.random.default_rng(0), 256)
+    for i in range(3):
+        abi.seb_sur_train_step(s.handle, 256, 1e-3, i + 1, 0)
+    torch.cuda.synchronize()
+
+
 def profile_sdf():
     """Three signed distance fields of the 400x400x72 fractal map's risk channel (obstacles
     risk >= 1, clamp 2 m) after one rebuild: the program ncu captures."""
@@ -411,6 +449,10 @@ def main():
         return profile_rebuild()
     if args.profile_sdf:
         return profile_sdf()
+    if args.profile_shift:
+        return profile_shift()
+    if args.profile_train:
+        return profile_train()
     if args.profile_surrogate:
         return profile_surrogate()
     if args.profile_query:

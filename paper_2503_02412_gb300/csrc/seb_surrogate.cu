@@ -274,17 +274,32 @@ __global__ void loss_partials_kernel(const float* __restrict__ pred, const float
 }
 
 // Sums the partials in a fixed order: tot[0] = loss (mean), tot[1] = count.
+// One block of 256 threads: thread t sums partials t, t + 256, ... in FP64, then a fixed-order
+// tree adds the 256 sums (deterministic: the same order every call).
 __global__ void loss_reduce_kernel(const float* __restrict__ partials, int nb, float* __restrict__ tot,
                                    float* __restrict__ loss_out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  __shared__ double ss[256], sc[256];
   double s = 0.0, c = 0.0;
-  for (int i = 0; i < nb; ++i) {
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     s += partials[2 * i];
     c += partials[2 * i + 1];
   }
-  tot[1] = (float)(c > 0 ? c : 1.0);
-  tot[0] = (float)(s / (c > 0 ? c : 1.0));
-  if (loss_out) *loss_out = tot[0];
+  ss[threadIdx.x] = s;
+  sc[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      ss[threadIdx.x] += ss[threadIdx.x + o];
+      sc[threadIdx.x] += sc[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double cc = sc[0] > 0 ? sc[0] : 1.0;
+    tot[1] = (float)cc;
+    tot[0] = (float)(ss[0] / cc);
+    if (loss_out) *loss_out = tot[0];
+  }
 }
 
 __global__ void dpred_kernel(const float* __restrict__ pred, const float* __restrict__ lab, int64_t n,
@@ -317,9 +332,10 @@ __global__ void head_bwd_dx_kernel(const float* __restrict__ dpred, const bf16* 
 // partial dwh[o, c] and dbh[o].
 constexpr int kSub = 64;     // pixels staged per shared-memory round
 constexpr int kChunkPx = 1024;  // pixels per CTA (one partial per CTA)
+constexpr int kHeadChunkPx = 256;  // head weight gradient: pixels per CTA
 
 __global__ void __launch_bounds__(256) head_bwd_dw_kernel(const float* __restrict__ dpred, const bf16* __restrict__ a,
-                                                          int64_t P, int nout, float* __restrict__ partials) {
+                                                          int64_t P, int nout, int chunk, float* __restrict__ partials) {
   extern __shared__ float sm[];
   float* gs = sm;                 // [kSub][nout]
   float* as = sm + kSub * nout;   // [kSub][kHid]
@@ -327,8 +343,8 @@ __global__ void __launch_bounds__(256) head_bwd_dw_kernel(const float* __restric
   const int per = (E + 255) / 256;
   float acc[24];
   for (int j = 0; j < per && j < 24; ++j) acc[j] = 0.f;
-  const int64_t p0 = (int64_t)blockIdx.x * kChunkPx;
-  for (int64_t q0 = p0; q0 < p0 + kChunkPx && q0 < P; q0 += kSub) {
+  const int64_t p0 = (int64_t)blockIdx.x * chunk;
+  for (int64_t q0 = p0; q0 < p0 + chunk && q0 < P; q0 += kSub) {
     const int np = (int)(P - q0 < kSub ? P - q0 : kSub);
     __syncthreads();
     for (int i = threadIdx.x; i < kSub * nout; i += blockDim.x) gs[i] = i < np * nout ? dpred[q0 * nout + i] : 0.f;
@@ -741,8 +757,50 @@ constexpr int kBdBOff = kTcBOff;                 // B after A (72 KB)
 constexpr int kBdBarOff = kBdBOff + 18 * 1024;
 constexpr int kBdSmem = kBdBarOff + 256;
 
-__global__ void __launch_bounds__(kTcM, 2) conv_bwd_dx_tc_kernel(const float* __restrict__ dy, const bf16* __restrict__ y,
-                                                                 const bf16* __restrict__ w, int B, int H, int W, int d,
+// dz = dy * (y > 0) split into BF16 hi = bf16(dz) and lo = bf16(dz - hi), written over dy in
+// place: pixel p's 128 bytes become [hi 0..31 | lo 0..31].  One thread per pixel.
+__global__ void split_dz_kernel(float* __restrict__ dy, const bf16* __restrict__ y, int64_t P) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  float g[kHid];
+  const float4* d4 = reinterpret_cast<const float4*>(dy + p * kHid);
+  const uint4* y4 = reinterpret_cast<const uint4*>(y + p * kHid);
+#pragma unroll
+  for (int q = 0; q < kHid / 8; ++q) {
+    const float4 a = d4[2 * q], b = d4[2 * q + 1];
+    const uint4 yv = y4[q];
+    const __nv_bfloat162* y2 = reinterpret_cast<const __nv_bfloat162*>(&yv);
+    const float gg[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const float ye = e & 1 ? __high2float(y2[e >> 1]) : __low2float(y2[e >> 1]);
+      g[8 * q + e] = ye > 0.f ? gg[e] : 0.f;
+    }
+  }
+  uint4* o4 = reinterpret_cast<uint4*>(dy + p * kHid);
+#pragma unroll
+  for (int q = 0; q < kHid / 8; ++q) {
+    float hi[8], lo[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      hi[e] = __bfloat162float(__float2bfloat16_rn(g[8 * q + e]));
+      lo[e] = g[8 * q + e] - hi[e];
+    }
+    o4[q] = pack8(hi);
+    o4[kHid / 8 + q] = pack8(lo);
+  }
+}
+
+// wt[c][tap][o] = w[o][tap][c] (the dgrad operand B in K-major order), one thread per element.
+__global__ void transpose_w_kernel(const bf16* __restrict__ w, bf16* __restrict__ wt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kHid * kTcK) return;
+  const int c = i / kTcK, k = i - c * kTcK, tap = k >> 5, o = k & 31;
+  wt[i] = w[((int64_t)o * 9 + tap) * kHid + c];
+}
+
+__global__ void __launch_bounds__(kTcM, 2) conv_bwd_dx_tc_kernel(const bf16* __restrict__ dzs,
+                                                                 const bf16* __restrict__ wt, int B, int H, int W, int d,
                                                                  float* __restrict__ dx, uint32_t* err) {
   extern __shared__ __align__(1024) uint8_t tsm[];
   uint8_t* As = tsm;
@@ -753,16 +811,11 @@ __global__ void __launch_bounds__(kTcM, 2) conv_bwd_dx_tc_kernel(const float* __
   const int Ho = H - 2 * d, Wo = W - 2 * d;
   const int64_t P = (int64_t)B * H * W;
   const int64_t p = (int64_t)blockIdx.x * kTcM + tid;
-  // B: K-major rows c, k = tap * 32 + o, value w[o][tap][c] (a transpose of the stored [o][tap][c])
+  // B: K-major rows c, k = tap * 32 + o; wt holds w transposed to [c][tap][o] (transpose_w_kernel)
   for (int i = tid; i < kHid * kTcKCores; i += kTcM) {
     const int c = i / kTcKCores, kc = i - c * kTcKCores;
-    float v[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int k = kc * 8 + e, tap = k >> 5, o = k & 31;
-      v[e] = __bfloat162float(w[((int64_t)o * 9 + tap) * kHid + c]);
-    }
-    *reinterpret_cast<uint4*>(Bs + tc_off(c, kc * 8, kHid / 8)) = pack8(v);
+    *reinterpret_cast<uint4*>(Bs + tc_off(c, kc * 8, kHid / 8)) =
+        reinterpret_cast<const uint4*>(wt + (int64_t)c * kTcK)[kc];
   }
   int b = 0, r = 0, s = 0;
   if (p < P) {
@@ -776,27 +829,23 @@ __global__ void __launch_bounds__(kTcM, 2) conv_bwd_dx_tc_kernel(const float* __
   const TcSync sync{mbar};
   bool ok = true;
   for (int part = 0; part < 2 && ok; ++part) {  // 0: hi, 1: lo
-    // A: this thread's row, 9 taps x 32 o of dz (part), 0 outside the output or past the last pixel
+    // A: this thread's row, 9 taps x 32 o of the split gradient (hi or lo half of the output
+    // pixel's 128 bytes), 16-byte copies, zero-filled outside the output or past the last pixel
 #pragma unroll 1
     for (int tap = 0; tap < 9; ++tap) {
       const int u = tap / 3, v = tap - u * 3;
       const int i = r - u * d, j = s - v * d;
       const bool in = p < P && i >= 0 && i < Ho && j >= 0 && j < Wo;
-      const int64_t q = in ? (((int64_t)b * Ho + i) * Wo + j) * kHid : 0;
+      const bf16* src = dzs + (in ? (((int64_t)b * Ho + i) * Wo + j) * 2 * kHid : 0) + part * kHid;
 #pragma unroll
-      for (int oc = 0; oc < 4; ++oc) {
-        float z[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int o = oc * 8 + e;
-          float g = 0.f;
-          if (in && __bfloat162float(y[q + o]) > 0.f) g = dy[q + o];
-          const float hi = __bfloat162float(__float2bfloat16_rn(g));
-          z[e] = part == 0 ? hi : g - hi;
-        }
-        *reinterpret_cast<uint4*>(As + tc_off(tid, tap * kHid + oc * 8, kTcM / 8)) = pack8(z);
-      }
+      for (int oc = 0; oc < 4; ++oc)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(As + tc_off(tid, tap * kHid + oc * 8,
+                                                                                                kTcM / 8))),
+                     "l"(src + oc * 8), "r"(in ? 16u : 0u)
+                     : "memory");
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands visible to the tensor core
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -834,9 +883,9 @@ __global__ void __launch_bounds__(kTcM, 2) conv_bwd_dx_tc_kernel(const float* __
 constexpr int kBwTile = kTcM * kTcM * 2;          // one A tile: 128 rows x 128 pixels BF16 (32 KB)
 constexpr int kBwBOff = 3 * kBwTile;              // B hi, then B lo: 32 rows x 128 pixels each (8 KB)
 constexpr int kBwBarOff = kBwBOff + 2 * kHid * kTcM * 2;
-constexpr int kBwSmem = kBwBarOff + 64 + kTcM * 4;  // + barrier, TMEM slot, pixel offsets: two CTAs per SM
+constexpr int kBwSmem = kBwBarOff + 64;  // + barrier and TMEM slot: two CTAs per SM
 
-__global__ void __launch_bounds__(kTcM, 2) conv_bwd_dw_tc_kernel(const float* __restrict__ dy, const bf16* __restrict__ y,
+__global__ void __launch_bounds__(kTcM, 2) conv_bwd_dw_tc_kernel(const bf16* __restrict__ dzs,
                                                                  const bf16* __restrict__ x, int B, int H, int W, int d,
                                                                  float* __restrict__ partials, uint32_t* err) {
   extern __shared__ __align__(1024) uint8_t tsm[];
@@ -844,7 +893,6 @@ __global__ void __launch_bounds__(kTcM, 2) conv_bwd_dw_tc_kernel(const float* __
   uint8_t* Bl = Bh + kHid * kTcM * 2;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(tsm + kBwBarOff);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(tsm + kBwBarOff + 16);
-  int32_t* poff = reinterpret_cast<int32_t*>(tsm + kBwBarOff + 64);  // x offset of each pixel, -1 past the end
   const int tid = threadIdx.x, warp = tid >> 5;
   const int Ho = H - 2 * d, Wo = W - 2 * d;
   const int64_t P = (int64_t)B * Ho * Wo;
@@ -855,60 +903,50 @@ __global__ void __launch_bounds__(kTcM, 2) conv_bwd_dw_tc_kernel(const float* __
   const int64_t p0 = (int64_t)blockIdx.x * kChunkPx;
   int round = 0;
   for (int64_t q0 = p0; q0 < p0 + kChunkPx && q0 < P && ok; q0 += kTcM, ++round) {
-    {  // this round's pixels
+    // Thread tid stages pixel k = tid of this round: column k of every operand row.  A rows
+    // m = tap * 32 + c take x at the pixel's tap offset (16-byte loads of the 32 channels); the
+    // ones row 288 is 1 for a pixel of the layer, 0 past the last one; rows 289..383 stay 0.
+    // B rows o take dz hi and lo (16-byte loads of the pixel's 32 gradients and activations).
+    {
       const int64_t p = q0 + tid;
-      int32_t off = -1;
-      if (p < P) {
+      const bool valid = p < P;
+      int64_t base = 0;
+      if (valid) {
         const int b = (int)(p / ((int64_t)Ho * Wo));
         const int rem = (int)(p - (int64_t)b * Ho * Wo);
         const int i = rem / Wo, j = rem - i * Wo;
-        off = (int32_t)((((int64_t)b * H + i) * W + j) * kHid);  // the host keeps B H W 32 below 2^31
+        base = (((int64_t)b * H + i) * W + j) * kHid;
       }
-      poff[tid] = off;
-    }
-    __syncthreads();
-    // A: thread tid writes row tid of each tile (m = 128 t + tid), all 128 pixels
+      bf16* sh = reinterpret_cast<bf16*>(tsm);
+      auto a_at = [&](int m) -> bf16& {  // element (m, k = tid) of the three stacked A tiles
+        return sh[((m >> 7) * kBwTile + tc_off(m & 127, tid, kTcM / 8)) / 2];
+      };
 #pragma unroll 1
-    for (int t = 0; t < 3; ++t) {
-      const int m = t * kTcM + tid;
-      const int tap = m >> 5, c = m & 31;
-      const int u = tap / 3, v = tap - u * 3;
-      const int64_t toff = ((int64_t)u * d * W + v * d) * kHid + c;
-      uint8_t* At = tsm + t * kBwTile;
-#pragma unroll 1
-      for (int kc = 0; kc < kTcM / 8; ++kc) {
-        float val[8];
+      for (int tap = 0; tap < 9; ++tap) {
+        const int u = tap / 3, v = tap - u * 3;
+        const uint4* src = reinterpret_cast<const uint4*>(x + base + ((int64_t)u * d * W + v * d) * kHid);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int32_t off = poff[kc * 8 + e];
-          float a = 0.f;
-          if (off >= 0) {
-            if (m < 9 * kHid)
-              a = __bfloat162float(x[off + toff]);
-            else if (m == 9 * kHid)
-              a = 1.f;  // the ones row: its D row is the bias gradient
-          }
-          val[e] = a;
+        for (int q = 0; q < 4; ++q) {
+          uint4 w8 = make_uint4(0u, 0u, 0u, 0u);
+          if (valid) w8 = src[q];
+          const bf16* e8 = reinterpret_cast<const bf16*>(&w8);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) a_at(tap * kHid + q * 8 + e) = e8[e];
         }
-        *reinterpret_cast<uint4*>(At + tc_off(tid, kc * 8, kTcM / 8)) = pack8(val);
       }
-    }
-    // B: rows o = tid & 31, pixel octets (tid >> 5) * 4 .. + 3, dz hi and lo
-    {
-      const int o = tid & 31;
-#pragma unroll 1
-      for (int kc = (tid >> 5) * 4; kc < (tid >> 5) * 4 + 4; ++kc) {
-        float hi[8], lo[8];
+      a_at(9 * kHid) = __float2bfloat16_rn(valid ? 1.f : 0.f);
+      if (round == 0)
+        for (int m = 9 * kHid + 1; m < 3 * kTcM; ++m) a_at(m) = __float2bfloat16_rn(0.f);
+      bf16* bh = reinterpret_cast<bf16*>(Bh);
+      bf16* bl = reinterpret_cast<bf16*>(Bl);
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int64_t p = q0 + kc * 8 + e;
-          float g = 0.f;
-          if (p < P && __bfloat162float(y[p * kHid + o]) > 0.f) g = dy[p * kHid + o];
-          hi[e] = __bfloat162float(__float2bfloat16_rn(g));
-          lo[e] = g - hi[e];
-        }
-        *reinterpret_cast<uint4*>(Bh + tc_off(o, kc * 8, kHid / 8)) = pack8(hi);
-        *reinterpret_cast<uint4*>(Bl + tc_off(o, kc * 8, kHid / 8)) = pack8(lo);
+      for (int q = 0; q < 8; ++q) {  // hi: q < 4, lo: q >= 4
+        uint4 w8 = make_uint4(0u, 0u, 0u, 0u);
+        if (valid) w8 = reinterpret_cast<const uint4*>(dzs + p * 2 * kHid)[q];
+        const bf16* e8 = reinterpret_cast<const bf16*>(&w8);
+        bf16* dst = q < 4 ? bh : bl;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) dst[tc_off((q & 3) * 8 + e, tid, kHid / 8) / 2] = e8[e];
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1404,17 +1442,22 @@ int seb_sur_train_step(seb_sur* h, int32_t B, float lr, int32_t step, float* los
   const bf16* wb = at<bf16>(h, h->v.weights_bf16);
   const int nb = grid_for(nl, 256) < 4096 ? grid_for(nl, 256) : 4096;
   loss_partials_kernel<<<nb, 256, 0, st>>>(pred, lab, nl, at<float>(h, h->v.loss_partials));
-  loss_reduce_kernel<<<1, 32, 0, st>>>(at<float>(h, h->v.loss_partials), nb, tot, loss_dev);
+  loss_reduce_kernel<<<1, 256, 0, st>>>(at<float>(h, h->v.loss_partials), nb, tot, loss_dev);
   dpred_kernel<<<grid_for(nl, 256), 256, 0, st>>>(pred, lab, nl, tot, dpred);
   // head
   head_bwd_dx_kernel<<<grid_for(P, 128), 128, 0, st>>>(dpred, wb + h->PL.wh, P, nout, at<float>(h, h->v.dact[3]));
   {
-    const int ch = chunks_for(P, kChunkPx);
+    // chunks of kHeadChunkPx pixels (4x more CTAs than kChunkPx): the head's P = B * 256 pixels
+    // would otherwise give too few CTAs; their partials fit the buffer sized for the first layer
     const int E = nout * kHid + nout;
+    const int64_t Emax = (int64_t)kHid * 9 * kHid + kHid > E ? (int64_t)kHid * 9 * kHid + kHid : E;
+    const int64_t cap = (int64_t)chunks_for((int64_t)h->max_batch * kSide[1] * kSide[1], kChunkPx) * Emax;
+    const int chunk = (int64_t)chunks_for(P, kHeadChunkPx) * E <= cap ? kHeadChunkPx : kChunkPx;
+    const int ch = chunks_for(P, chunk);
     if ((E + 255) / 256 > 24) return fail("surrogate head too wide for the weight-gradient kernel");
     const size_t shm = (size_t)kSub * (nout + kHid) * sizeof(float);
     cudaFuncSetAttribute(head_bwd_dw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    head_bwd_dw_kernel<<<ch, 256, shm, st>>>(dpred, at<bf16>(h, h->v.act[3]), P, nout, part);
+    head_bwd_dw_kernel<<<ch, 256, shm, st>>>(dpred, at<bf16>(h, h->v.act[3]), P, nout, chunk, part);
     reduce_partials_kernel<<<grid_for(E, 256), 256, 0, st>>>(part, ch, E, grad + h->PL.wh);
   }
   // conv layers, last to first; dact[l] holds d loss / d (output of layer l)
@@ -1431,12 +1474,19 @@ int seb_sur_train_step(seb_sur* h, int32_t B, float lr, int32_t step, float* los
       reduce_partials_kernel<<<grid_for(E, 256), 256, 0, st>>>(part, ch, E, grad + h->PL.w[0]);
     } else if (h->engine == SEB_SUR_TCGEN05) {
       const int E = kHid * 9 * kHid + kHid;
+      // the upstream gradient, masked by this layer's ReLU and split into BF16 hi / lo, over itself
+      float* dyw = at<float>(h, h->v.dact[l]);
+      split_dz_kernel<<<grid_for(Po, 128), 128, 0, st>>>(dyw, y, Po);
+      const bf16* dzs = reinterpret_cast<const bf16*>(dyw);
       cudaFuncSetAttribute(conv_bwd_dw_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBwSmem);
-      conv_bwd_dw_tc_kernel<<<ch, kTcM, kBwSmem, st>>>(dy, y, xin, B, S, S, d, part, h->err);
+      conv_bwd_dw_tc_kernel<<<ch, kTcM, kBwSmem, st>>>(dzs, xin, B, S, S, d, part, h->err);
       reduce_partials_kernel<<<grid_for(E, 256), 256, 0, st>>>(part, ch, E, grad + h->PL.w[l]);
+      // the weight partials have been summed: their buffer holds the transposed weights now
+      bf16* wt = reinterpret_cast<bf16*>(part);
+      transpose_w_kernel<<<grid_for(kHid * kTcK, 256), 256, 0, st>>>(wb + h->PL.w[l], wt);
       cudaFuncSetAttribute(conv_bwd_dx_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBdSmem);
       conv_bwd_dx_tc_kernel<<<(unsigned)(((int64_t)B * S * S + kTcM - 1) / kTcM), kTcM, kBdSmem, st>>>(
-          dy, y, wb + h->PL.w[l], B, S, S, d, at<float>(h, h->v.dact[l - 1]), h->err);
+          dzs, wt, B, S, S, d, at<float>(h, h->v.dact[l - 1]), h->err);
     } else {
       const int E = kHid * 9 * kHid + kHid;
       conv_bwd_dw_kernel<kHid><<<ch, 256, 0, st>>>(dy, y, xin, B, S, S, d, part);
