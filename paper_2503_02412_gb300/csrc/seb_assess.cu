@@ -71,7 +71,8 @@ __device__ __forceinline__ float stage_elev<Bf16Tiled>(const Launch& L, Bf16Tile
 // pitch/roll at heading (ct, st), fitted-plane height at the cell centre, risk.
 __device__ __noinline__ Cell finish_cell(int N, int MX, int MY, int MXX, int MXY, int MYY, float S0,
                                          float S1, float S2, float S3, float ref, int n_min,
-                                         float ct, float st, const Launch& L) {
+                                         float ct, float st, const Launch& L, int n_full = 0,
+                                         float inv_n_full = 0.f) {
   Cell o;
   const float qnan = __int_as_float(0x7fc00000);
   if (N < n_min) {
@@ -82,7 +83,9 @@ __device__ __noinline__ Cell finish_cell(int N, int MX, int MY, int MXX, int MXY
   }
   const float res = L.res;
   const float fN = (float)N;
-  const float iN = 1.f / fN;  // exact reciprocal: the means use it
+  // exact reciprocal (the means use it); a complete footprint takes the table's 1/N, the same
+  // correctly rounded value the division gives
+  const float iN = N == n_full ? inv_n_full : 1.f / fN;
   const float inv_n2 = iN * iN;
   // N^2 Cov_xy-block numerators are exact integers (int32 when the tables allow it: 64-bit
   // integer conversions run on the FP64 unit).
@@ -570,13 +573,10 @@ __global__ void __launch_bounds__(kThreads, 2)
         ++row;
       }
     }
-    __syncthreads();
+    __syncthreads();  // the box (in qs) is consumed: each thread's own qs slots are zeroed when first used
     if (tid == 0) mbar_inval(bar);
-    for (int i = tid; i < kSlQ * kThreads; i += kThreads) qs[i] = make_float2(0.f, 0.f);
-    __syncthreads();
   } else {
     for (int i = tid; i < sh; i += kThreads) rowflag[i] = 0;
-    for (int i = tid; i < kSlQ * kThreads; i += kThreads) qs[i] = make_float2(0.f, 0.f);
     __syncthreads();
     int row = tid / sw, col = tid - (tid / sw) * sw;
     while (row < sh) {
@@ -641,6 +641,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
   for (int t = 0; t < 3; ++t) D0[t] = D1[t] = D2[t] = D3[t] = E0[t] = E1[t] = E2[t] = E3[t] = zero2;
   auto Qs = [&](int k, int g) -> float2& { return qs[(k * 4 + g) * kThreads + tid]; };
+  bool qdirty = false;  // this thread's Qs slots hold moments (a masked run happened)
 
   for (int q = r0; q < r1; ++q) {
     const uint32_t pk = T.runs[q];
@@ -702,6 +703,13 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
       for (int t = 0; t < 3; ++t) slide(t, add2(pq[t], nref), add2(pq[len + t], nref));
     } else {
+      if (!qdirty) {  // this thread's missing-point moments start at zero (its own slots only)
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+#pragma unroll
+          for (int g = 0; g < 4; ++g) Qs(k, g) = zero2;
+        qdirty = true;
+      }
       // unknown heights: weight m = 0, z' = fma(-ref, m, z) = 0; x = 1 - m counts them
       auto zof = [&](int k, float2& zp, float2& x) {
         const float2 v = pq[k];
@@ -814,12 +822,15 @@ __global__ void __launch_bounds__(kThreads, 2)
       const int c = cx + g;
       keep[g] = stores(c, r) && (!L.store_mask || L.store_mask[(int64_t)r * L.nx + c]);
       if (!keep[g]) continue;
-      float qv[6];
+      float qv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (qdirty) {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) qv[k] = h ? Qs(k, g).y : Qs(k, g).x;
+        for (int k = 0; k < 6; ++k) qv[k] = h ? Qs(k, g).y : Qs(k, g).x;
+      }
       o[g] = finish_cell(mom[0] - (int)qv[0], mom[1] - (int)qv[1], mom[2] - (int)qv[2], mom[3] - (int)qv[3],
                          mom[4] - (int)qv[4], mom[5] - (int)qv[5], h ? S0[g].y : S0[g].x, h ? S1[g].y : S1[g].x,
-                         h ? S2[g].y : S2[g].x, h ? S3[g].y : S3[g].x, ref, T.n_min[pair], ct, st, L);
+                         h ? S2[g].y : S2[g].x, h ? S3[g].y : S3[g].x, ref, T.n_min[pair], ct, st, L, mom[0],
+                         T.inv_n[pair]);
     }
     int pc = cx + L.ring_x;
     if (pc >= L.nx) pc -= L.nx;

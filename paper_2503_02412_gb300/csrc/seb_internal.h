@@ -42,6 +42,7 @@ struct Tables {
   int32_t rx, ry;                    // largest |di| / |dj| over every footprint
   int32_t run_start[kMaxPairs + 1];  // runs of pair p: [run_start[p], run_start[p+1])
   int32_t n_min[kMaxPairs];          // known cells needed to assess (per bin)
+  float inv_n[kMaxPairs];            // 1 / N of the complete footprint, correctly rounded
   int32_t mom[kMaxPairs][6];         // N, sum di, sum dj, sum di^2, sum di dj, sum dj^2
   float cos_t[kMaxPairs], sin_t[kMaxPairs];  // heading of bin p (bin p + K/2 negates both)
   uint32_t runs[kMaxRuns];           // packed (dj + 128) | (lo + 128) << 8 | (hi + 128) << 16

@@ -116,6 +116,7 @@ int build_tables(const seb_params& p, Tables* T, int32_t* total_runs) {
       T->mom[q][t] = (int32_t)m[t];
     }
     T->n_min[q] = p.n_min > 0 ? p.n_min : ((n + 1) / 2 > 3 ? (n + 1) / 2 : 3);
+    T->inv_n[q] = n > 0 ? 1.0f / (float)n : 0.f;  // IEEE division: the value 1.f / N gives on the GPU
     const double th = 2.0 * M_PI * (double)q / (double)p.n_yaw;
     T->cos_t[q] = (float)cos(th);
     T->sin_t[q] = (float)sin(th);
