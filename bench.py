@@ -44,7 +44,7 @@ METRIC = "SE(2) cells/s (400x400x72 map: full rebuild + 50 rolling shifts per st
 
 # ncu DRAM traffic of one full-map rebuild launch (dram__bytes_read.sum + dram__bytes_write.sum),
 # valid only for the kernel source it was captured on (hash of the assess kernel's sources).
-NCU_TRAFFIC = {"sources_sha": "bcb0e953eff13687", "bytes": 725760 + 188623872}
+NCU_TRAFFIC = {"sources_sha": "0ce335e67b7ff3e1", "bytes": 731136 + 188180480}
 
 
 def algorithmic_flop_per_cell(table):
@@ -665,8 +665,17 @@ def measure_rows(seb, args, dev, acc_jobs=None):
     bwd = lambda: abi.seb_query_poses_backward(c, e.data_ptr(), 0, 0, poses.data_ptr(), sv.data_ptr(),  # noqa: E731
                                                g.data_ptr(), gp.data_ptr(), n, st.cuda_stream)
     tf, tb = _time(fwd, 10, st), _time(bwd, 10, st)
+    # the query gathers 4 bilinear corners per lattice point from the L2-resident 40 KB map: its
+    # roofline is the L2 (and L1) read bandwidth, measured here by summing an L2-resident buffer
+    l2 = l2_read_gbs(dev, st)
+    n_lat = len(abi.seb_footprint_table(c, 0))
+    gather = n * n_lat * 4 * 4  # bytes of corner heights read per forward
     rows["query_1M_poses"] = {"fwd_ms": tf, "bwd_ms": tb, "fwd_poses_per_s": n / tf * 1e3,
-                              "bwd_poses_per_s": n / tb * 1e3, "config": "100x100 map at 0.1 m, 0.6x0.4 m"}
+                              "bwd_poses_per_s": n / tb * 1e3, "config": "100x100 map at 0.1 m, 0.6x0.4 m",
+                              "roofline": {"bound": "l2", "gather_bytes_fwd": gather,
+                                           "achieved_gbs_fwd": gather / (tf * 1e-3) / 1e9, "peak_gbs": l2,
+                                           "frac_fwd": gather / (tf * 1e-3) / 1e9 / l2,
+                                           "peak_basis": "measured: L2-resident 16 MB copy, read + write bytes"}}
     # trilinear SE(2) lookup of the grid at the same poses, against the exact query
     abi.seb_query_poses(c, e.data_ptr(), 0, 0, poses.data_ptr(), n, out.data_ptr(), fl.data_ptr(), 0, st.cuda_stream)
     mq = seb.SebMap(pq, dev)
@@ -811,6 +820,19 @@ def measure_rows(seb, args, dev, acc_jobs=None):
             "basis": "algorithmic FLOP of the tcgen05 layers over the whole forward / train-step time (the first "
                      "layer, the head, the loss and Adam run on CUDA cores inside the same time)"}}
     return rows
+
+
+def l2_read_gbs(dev, st, mb=16, reps=100):
+    """Throughput of the L2 cache: a 16 MB float buffer copied into another (both L2-resident
+    after the first pass) reps times, bytes read plus written over CUDA-event time."""
+    import torch
+
+    a = torch.ones(mb * 1024 * 1024 // 4, device=dev)
+    b = torch.empty_like(a)
+    for _ in range(3):
+        b.copy_(a)
+    t = _time(lambda: b.copy_(a), reps, st)
+    return 2 * a.numel() * 4 / (t * 1e-3) / 1e9
 
 
 def measured_peak(key, fallback):
