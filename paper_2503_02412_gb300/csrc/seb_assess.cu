@@ -344,7 +344,6 @@ __global__ void __launch_bounds__(kThreads, 2)
   for (int i = threadIdx.x; i < sh; i += kThreads) rowflag[i] = 0;
   __syncthreads();
   // Stage tile + halo (outside the window = NaN = unknown).
-  const E* __restrict__ elev = static_cast<const E*>(L.elev);
   const float qnan = __int_as_float(0x7fc00000);
   for (int idx = threadIdx.x; idx < sw * sh; idx += kThreads) {
     const int row = idx / sw, col = idx - row * sw;
@@ -455,10 +454,10 @@ __host__ __device__ inline int sl_tw(int lay) { return 4 << lay; }
 __host__ __device__ inline int sl_th(int lay) { return 2 * (kThreads >> lay); }
 __host__ __device__ inline int sl_sw2(int lay, int rx) { return (sl_tw(lay) + 2 * rx + 3 + 7) & ~7; }
 __device__ __forceinline__ int sl_index(int r, int c, int sw2) { return r * sw2 + c + ((r >> 1) & 3); }
-constexpr int kSlQ = 6 * 4;  // missing-point moments per thread: [k][g] float2 (rows packed)
+constexpr int kSlQ = 6 * 4;  // missing-point moments per thread: [k][g], both rows in one int32
 
 // Tensor maps of the elevation for the TMA staging, one per tile layout (index stage_map()).
-struct alignas(64) StageMaps {
+struct StageMaps {
   CUtensorMap map[3];
 };
 __host__ __device__ inline int stage_map(int lay) { return lay == 2 ? 0 : (lay == 3 ? 1 : 2); }
@@ -488,7 +487,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                      const __grid_constant__ StageMaps SM) {
   extern __shared__ float smem[];
   int* rowflag = reinterpret_cast<int*>(smem);
-  float2* qs = reinterpret_cast<float2*>(smem + kMaxStageRows);  // [kSlQ][kThreads]
+  float2* qs = reinterpret_cast<float2*>(smem + kMaxStageRows);  // TMA box scratch: kSlQ x kThreads slots
   float2* pt = qs + kSlQ * kThreads;                             // [sh - 1][sw2] vertical pairs
   // No global memory access before the stream's previous kernel has completed (pdl_entry) ...
   // except in a later launch of one shift batch: its input window was written before the batch
@@ -517,7 +516,6 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int sw = tw + 2 * rx, sh = th + 2 * ry, sw2 = sl_sw2(lay, rx);
   const int tid = threadIdx.x;
 
-  const E* __restrict__ elev = static_cast<const E*>(L.elev);
   const float qnan = __int_as_float(0x7fc00000);
   // Each staged value v goes to two vertical pairs: (row, row + 1).x and (row - 1, row).y.
   auto put = [&](int row, int col, float v) {
@@ -533,7 +531,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     // Tile + halo in one TMA copy into the CTA's shared memory (Algorithm 1's footprint cells
     // of every cell of the tile; outside the window the map's fill value NaN = unknown, as in
     // Sec. V-A).  The box starts at the staged tile's first column rounded down to 16 bytes and
-    // lands in the moment scratch qs, which is zeroed only after the repack below.
+    // lands in the scratch qs.
     constexpr int q = 16 / (int)sizeof(E);
     const int gx0 = tx0 - rx, gy0 = ty0 - ry;
     const int x0a = gx0 >= 0 ? gx0 / q * q : -((q - 1 - gx0) / q) * q;
@@ -573,7 +571,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         ++row;
       }
     }
-    __syncthreads();  // the box (in qs) is consumed: each thread's own qs slots are zeroed when first used
+    __syncthreads();  // the box (in qs) is consumed
     if (tid == 0) mbar_inval(bar);
   } else {
     for (int i = tid; i < sh; i += kThreads) rowflag[i] = 0;
@@ -640,10 +638,35 @@ __global__ void __launch_bounds__(kThreads, 2)
   float2 E0[3], E1[3], E2[3], E3[3];
 #pragma unroll
   for (int t = 0; t < 3; ++t) D0[t] = D1[t] = D2[t] = D3[t] = E0[t] = E1[t] = E2[t] = E3[t] = zero2;
-  auto Qs = [&](int k, int g) -> float2& { return qs[(k * 4 + g) * kThreads + tid]; };
-  bool qdirty = false;  // this thread's Qs slots hold moments (a masked run happened)
+  // Integer moments of the missing points of the 8 cells, Qp[k][g] for column g: k = 0..5 ->
+  // (n, sum di, sum dj, sum di^2, sum di dj, sum dj^2).  Both rows of a column share one int32,
+  // row 0 + 65536 x row 1 (two's complement): sums of such words are exact as long as every
+  // field stays within [-32768, 32767].  Each field is a moment of a subset of the footprint, so
+  // it is bounded by (points summed) x reach^2; when a whole footprint can exceed the range, the
+  // words are unpacked into int32 sums in the (then free) box scratch every L.q_flush runs.
+  int Qp[kSlQ];
+#pragma unroll
+  for (int i = 0; i < kSlQ; ++i) Qp[i] = 0;
+  int* qsi = reinterpret_cast<int*>(qs);  // [2 kSlQ][kThreads] int32 sums, or [kSlQ][kThreads] words
+  bool qflushed = false;
+  auto flush = [&]() {
+#pragma unroll
+    for (int i = 0; i < kSlQ; ++i) {
+      const int w = Qp[i], a = (w << 16) >> 16, b = (w - a) >> 16;  // row 0: the sign-extended low half
+      qsi[(2 * i) * kThreads + tid] = (qflushed ? qsi[(2 * i) * kThreads + tid] : 0) + a;
+      qsi[(2 * i + 1) * kThreads + tid] = (qflushed ? qsi[(2 * i + 1) * kThreads + tid] : 0) + b;
+      Qp[i] = 0;
+    }
+    qflushed = true;
+  };
 
-  for (int q = r0; q < r1; ++q) {
+  // the runs in chunks of L.q_flush (all of them when 0); the packed words are flushed between
+  // chunks (the same runs in every thread of the CTA)
+  const int chunk = L.q_flush > 0 ? L.q_flush : (r1 > r0 ? r1 - r0 : 1);
+  for (int q0 = r0; q0 < r1; q0 += chunk) {
+  if (q0 > r0) flush();
+  const int q1 = q0 + chunk < r1 ? q0 + chunk : r1;
+  for (int q = q0; q < q1; ++q) {
     const uint32_t pk = T.runs[q];
     const int dj = unpack(pk, 0), lo = unpack(pk, 8), hi = unpack(pk, 16);
     const int row = ry + ly + dj;
@@ -703,76 +726,68 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
       for (int t = 0; t < 3; ++t) slide(t, add2(pq[t], nref), add2(pq[len + t], nref));
     } else {
-      if (!qdirty) {  // this thread's missing-point moments start at zero (its own slots only)
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-#pragma unroll
-          for (int g = 0; g < 4; ++g) Qs(k, g) = zero2;
-        qdirty = true;
-      }
-      // unknown heights: weight m = 0, z' = fma(-ref, m, z) = 0; x = 1 - m counts them
-      auto zof = [&](int k, float2& zp, float2& x) {
+      // unknown heights: z' = 0 (the known ones get exactly the plain path's z - ref); the packed
+      // word u = [x unknown] + 65536 [y unknown] counts them for both rows at once
+      constexpr int kP = 0x10001;
+      auto zof = [&](int k, float2& zp, int& u) {
         const float2 v = pq[k];
         const bool kx = v.x == v.x, ky = v.y == v.y;
-        const float2 m = f2(kx ? 1.f : 0.f, ky ? 1.f : 0.f);
-        zp = fma2(nref, m, f2(kx ? v.x : 0.f, ky ? v.y : 0.f));
-        x = f2(kx ? 0.f : 1.f, ky ? 0.f : 1.f);
+        const float2 zr = add2(v, nref);
+        zp = f2(kx ? zr.x : 0.f, ky ? zr.y : 0.f);
+        u = (kx ? 0 : 1) + (ky ? 0 : 0x10000);
       };
       // Known weights summed three times over (k1 = sum m, k2 = sum (len - k) m_k,
-      // k3 = sum (len - k)(len - k + 1) / 2 m_k); with u = len - k the missing moments are
-      // X1 = len - k1, X2 = sum u x = len (len + 1) / 2 - k2, X3 = len (len + 1)(len + 2) / 6 - k3,
-      // and p = hi + 1 - u gives qx = (hi + 1) X1 - X2, qxx = (hi + 1)^2 X1 - 2 (hi + 1) X2 + 2 X3 - X2.
-      // Every term is an integer below 2^24, so all of it is exact.
+      // k3 = sum (len - k)(len - k + 1) / 2 m_k, packed like Qp); with u = len - k the missing
+      // moments are X1 = len - k1, X2 = sum u x = len (len + 1) / 2 - k2,
+      // X3 = len (len + 1)(len + 2) / 6 - k3, and p = hi + 1 - u gives qx = (hi + 1) X1 - X2,
+      // qxx = (hi + 1)^2 X1 - 2 (hi + 1) X2 + 2 X3 - X2.
       float2 Ab = zero2, Tb = zero2, Cb = zero2;
-      float2 k1 = zero2, k2 = zero2, k3 = zero2;
+      int k1 = 0, k2 = 0, k3 = 0;
 #pragma unroll 2
       for (int k = 0; k < len; ++k) {
         const float2 v = pq[k];
         const bool kx = v.x == v.x, ky = v.y == v.y;
-        const float2 m = f2(kx ? 1.f : 0.f, ky ? 1.f : 0.f);
-        const float2 zp = fma2(nref, m, f2(kx ? v.x : 0.f, ky ? v.y : 0.f));
+        const float2 zr = add2(v, nref);
+        const float2 zp = f2(kx ? zr.x : 0.f, ky ? zr.y : 0.f);
         Ab = add2(Ab, zp);
         Tb = add2(Tb, Ab);
         Cb = fma2(zp, zp, Cb);
-        k1 = add2(k1, m);
-        k2 = add2(k2, k1);
-        k3 = add2(k3, k2);
+        k1 += (kx ? 1 : 0) + (ky ? 0x10000 : 0);
+        k2 += k1;
+        k3 += k2;
       }
       column0(Ab, fma2(H2, Ab, neg2(Tb)), Cb);
-      const float fl = (float)len;
-      const float t1 = fl, t2 = fl * (fl + 1.f) * 0.5f, t3 = (float)(len * (len + 1) * (len + 2) / 6);
-      const float2 X1 = add2(f2(t1, t1), neg2(k1)), X2 = add2(f2(t2, t2), neg2(k2)),
-                   X3 = add2(f2(t3, t3), neg2(k3));
-      float2 qn = X1;
-      float2 qx = fma2(H2, X1, neg2(X2));
-      float2 qxx = add2(fma2(__fmul2_rn(H2, H2), X1, fma2(f2(-2.f * h1, -2.f * h1), X2, add2(X3, X3))), neg2(X2));
-      const float fdj = (float)dj;
-      const float2 dj22 = f2(fdj * fdj, fdj * fdj);
+      const int H = hi + 1;
+      const int X1 = len * kP - k1, X2 = (len * (len + 1) / 2) * kP - k2,
+                X3 = (len * (len + 1) * (len + 2) / 6) * kP - k3;
+      int qn = X1;
+      int qx = H * X1 - X2;
+      int qxx = H * H * X1 - 2 * H * X2 + 2 * X3 - X2;
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
         if (g > 0) {
-          float2 zo, xo, zi, xi;
+          float2 zo, zi;
+          int xo, xi;
           zof(g - 1, zo, xo);
           zof(len - 1 + g, zi, xi);
           slide(g - 1, zo, zi);
-          const float po = flo + (float)(g - 1), pi = fhi + (float)g;
-          const float2 po2 = f2(po, po), pi2 = f2(pi, pi);
-          qn = add2(add2(qn, neg2(xo)), xi);
-          qx = fma2(pi2, xi, fma2(neg2(po2), xo, qx));
-          qxx = fma2(__fmul2_rn(pi2, pi2), xi, fma2(neg2(__fmul2_rn(po2, po2)), xo, qxx));
+          const int po = lo + g - 1, pi = hi + g;
+          qn += xi - xo;
+          qx += pi * xi - po * xo;
+          qxx += pi * pi * xi - po * po * xo;
         }
         // missing-point moments of column g in its own offsets di = p - g
-        const float fg = (float)g;
-        const float2 sdi = fma2(f2(-fg, -fg), qn, qx);
-        const float2 sdi2 = fma2(f2(fg * fg, fg * fg), qn, fma2(f2(-2.f * fg, -2.f * fg), qx, qxx));
-        Qs(0, g) = add2(Qs(0, g), qn);
-        Qs(1, g) = add2(Qs(1, g), sdi);
-        Qs(2, g) = fma2(dj2, qn, Qs(2, g));
-        Qs(3, g) = add2(Qs(3, g), sdi2);
-        Qs(4, g) = fma2(dj2, sdi, Qs(4, g));
-        Qs(5, g) = fma2(dj22, qn, Qs(5, g));
+        const int sdi = qx - g * qn;
+        const int sdi2 = qxx - 2 * g * qx + g * g * qn;
+        Qp[0 * 4 + g] += qn;
+        Qp[1 * 4 + g] += sdi;
+        Qp[2 * 4 + g] += dj * qn;
+        Qp[3 * 4 + g] += sdi2;
+        Qp[4 * 4 + g] += dj * sdi;
+        Qp[5 * 4 + g] += dj * dj * qn;
       }
     }
+  }
   }
   if (COMP) {  // fold the compensations in: the exact sum is s - c
     S0c = add2(S0c, neg2(K0));
@@ -805,6 +820,14 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
   }
 
+  // the missing-point moments wait for the finish in the (now free) box scratch, out of registers
+  if (qflushed) {
+    flush();
+  } else {
+#pragma unroll
+    for (int i = 0; i < kSlQ; ++i) qsi[i * kThreads + tid] = Qp[i];
+  }
+
   if (L.early) asm volatile("griddepcontrol.wait;" ::: "memory");  // the previous launch's stores first
   const int k0 = pair, k1 = pair + T.n_pairs;
   const float ct = T.cos_t[pair], st = T.sin_t[pair];
@@ -822,13 +845,18 @@ __global__ void __launch_bounds__(kThreads, 2)
       const int c = cx + g;
       keep[g] = stores(c, r) && (!L.store_mask || L.store_mask[(int64_t)r * L.nx + c]);
       if (!keep[g]) continue;
-      float qv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      if (qdirty) {
+      int qv[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) qv[k] = h ? Qs(k, g).y : Qs(k, g).x;
+      for (int k = 0; k < 6; ++k) {
+        if (qflushed) {
+          qv[k] = qsi[(2 * (k * 4 + g) + h) * kThreads + tid];
+        } else {
+          const int w = qsi[(k * 4 + g) * kThreads + tid], a = (w << 16) >> 16;  // row 0: the low half
+          qv[k] = h ? (w - a) >> 16 : a;
+        }
       }
-      o[g] = finish_cell(mom[0] - (int)qv[0], mom[1] - (int)qv[1], mom[2] - (int)qv[2], mom[3] - (int)qv[3],
-                         mom[4] - (int)qv[4], mom[5] - (int)qv[5], h ? S0[g].y : S0[g].x, h ? S1[g].y : S1[g].x,
+      o[g] = finish_cell(mom[0] - qv[0], mom[1] - qv[1], mom[2] - qv[2], mom[3] - qv[3],
+                         mom[4] - qv[4], mom[5] - qv[5], h ? S0[g].y : S0[g].x, h ? S1[g].y : S1[g].x,
                          h ? S2[g].y : S2[g].x, h ? S3[g].y : S3[g].x, ref, T.n_min[pair], ct, st, L, mom[0],
                          T.inv_n[pair]);
     }
@@ -1032,6 +1060,19 @@ bool stage_maps(const Tables& T, const Launch& L, StageMaps* M) {
   return true;
 }
 
+// The sliding kernel packs the missing-point moments of a block's two rows into one int32 per
+// moment.  Every field is a moment (n, sums of di, dj, di^2, di dj, dj^2) of a subset of one
+// footprint, so |field| <= points x reach^2.  Returns the runs after which the packed words must
+// be flushed (0: a whole footprint fits int16, never), or -1 when not even one run fits.
+int packed_moment_flush(const Tables& T) {
+  const long long r = T.rx > T.ry ? T.rx : T.ry, w = r * r > 1 ? r * r : 1;
+  long long n_max = 0;
+  for (int p = 0; p < T.n_pairs; ++p) n_max = T.mom[p][0] > n_max ? T.mom[p][0] : n_max;
+  if (n_max * w <= 32767) return 0;
+  const long long per_run = (2 * T.rx + 1) * w;  // a run holds at most 2 rx + 1 points
+  return per_run <= 32767 ? (int)(32767 / per_run) : -1;
+}
+
 template <typename E, bool COMP>
 cudaError_t launch_typed(const Tables& T, const Launch& Lreq, cudaStream_t stream) {
   Launch L = Lreq;
@@ -1042,7 +1083,8 @@ cudaError_t launch_typed(const Tables& T, const Launch& Lreq, cudaStream_t strea
     L.vec4 = (L.nx % 4 == 0) && ((uintptr_t)L.out % 16 == 0) && ((uintptr_t)L.flags % 4 == 0);
     const size_t smem = smem_sl(T, L);
     L.pairs_alloc = (int32_t)pairs_sl(T, L);
-    if (smem <= 227 * 1024) {
+    L.q_flush = packed_moment_flush(T);
+    if (smem <= 227 * 1024 && L.q_flush >= 0) {
       if (L.tile_start[L.n_rects] == 0) return cudaSuccess;
       StageMaps M;
       L.tma = stage_maps<E>(T, L, &M) ? 1 : 0;

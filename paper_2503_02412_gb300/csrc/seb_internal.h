@@ -77,6 +77,7 @@ struct Launch {
   int32_t tma;               // stage the tile with one TMA copy per CTA (set by the launcher)
   int32_t all_masked;        // every row run takes the masked moment path (rolling-shift bands)
   int32_t pairs_alloc;       // float2 slots of the staged vertical pairs (bounds checks of SEB_DEBUG builds)
+  int32_t q_flush;           // row runs after which the packed missing-point moments are flushed (0: never)
   // SEB_BF16_TILED windows: the FP32 bases [TY][TX] and the window's phase in the 16-cell tiles
   const float* tile_base;
   int32_t base_tx, base_px, base_py;

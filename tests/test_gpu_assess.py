@@ -189,6 +189,32 @@ def test_large_footprint_per_cell_kernel(seb):
     assert s["assessed"] > 0.5 * s["n"]
 
 
+FLUSH = dict(nx=96, ny=72, n_yaw=4, res=0.05, length=1.3, width=0.9)
+
+
+def test_packed_moment_flush(seb):
+    """A 1.3 x 0.9 m footprint at 0.05 m (reach 16 cells, ~470 points per cell): the moments of a
+    whole footprint's missing points overflow the 16-bit fields that the sliding kernel packs
+    the two rows of a block into, so the packed sums are moved into 32-bit sums every few row
+    runs.  Every cell equals the oracle, and a rolling shift equals a rebuild bit for bit."""
+    e = fractal_steps_nan(5, 96, 72, res=0.05, nan_frac=0.05)
+    _, out, fl, _ = run_map(seb, FLUSH, e)
+    s = check(out, fl, oracle_grid(FLUSH, e), "flushed moments")
+    assert s["assessed"] > 0.5 * s["n"]
+    world = torch.from_numpy(fractal_world(6, 300)).cuda()
+    win = lambda o: world[o[1]:o[1] + 72, o[0]:o[0] + 96].contiguous()  # noqa: E731
+    p = seb.SebParams(**FLUSH)
+    m = seb.SebMap(p)
+    m.update(win((100, 100)), (100, 100))
+    for o in [(104, 97), (93, 99), (93, 120)]:
+        m.shift(win(o), o)
+    full = seb.SebMap(p)
+    full.update(win((93, 120)), (93, 120))
+    a, af = m.outputs()
+    b, bf = full.outputs()
+    assert torch.equal(a.view(torch.int32), b.view(torch.int32)) and torch.equal(af, bf)
+
+
 def test_rolling_window_bit_identical_to_rebuild(seb):
     """Sec. V-A: the window follows the robot; after 50 moves of 10 cells in random
     directions the ring-buffered map equals a fresh rebuild of the final window, bit for bit,
