@@ -441,26 +441,47 @@ __global__ void __launch_bounds__(kThreads, 2)
 //   C_g = C_{g-1} - z'(lo+g-1)^2 + z'(hi+g)^2, and sum di z' = Bx_g - g A_g for column g.
 // Runs whose rows (over the warp) hold an unknown cell use weights m (z' = fma(-ref, m, z)) and
 // slide the moments of the missing points the same way; both paths give bit-identical sums
-// for runs without unknown cells.  Alternate pair rows are skewed so that a half-warp (4 blocks
-// x 4 pair rows) reads 32 distinct banks.
-// Layouts (log2 of blocks per row): 3 -> 32 x 64 cells, 2 -> 16 x 128, 5 -> 128 x 16.
+// for runs without unknown cells.
+// Layouts.  Quad layouts (log2 of blocks per row): 3 -> 32 x 64 cells, 2 -> 16 x 128, 5 -> 128 x 16;
+// a half-warp holds 4 blocks x 4 block rows, and alternate pair rows are skewed so that its
+// 8-byte reads hit 16 distinct slots (32 banks).  Column layouts kColLay + W (W = 3 or 5 blocks
+// per row, 80 or 48 block rows) tile the column bands of a rolling shift that are 12 or 20 cells
+// wide without computing cells outside them: thread t holds block column t / H, block row t % H,
+// so a half-warp reads 16 pair rows 2 apart in one column; an odd row stride (in 8-byte slots) and
+// a one-slot skew every 16 rows keep those 16 reads distinct.
 // ------------------------------------------------------------------------------------------------
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 neg2(float2 a) { return f2(-a.x, -a.y); }
 
-__host__ __device__ inline int sl_tw(int lay) { return 4 << lay; }
-__host__ __device__ inline int sl_th(int lay) { return 2 * (kThreads >> lay); }
-__host__ __device__ inline int sl_sw2(int lay, int rx) { return (sl_tw(lay) + 2 * rx + 3 + 7) & ~7; }
-__device__ __forceinline__ int sl_index(int r, int c, int sw2) { return r * sw2 + c + ((r >> 1) & 3); }
+constexpr int kColLay = 16;
+__host__ __device__ inline bool sl_col(int lay) { return lay >= kColLay; }
+// blocks per row and block rows of a tile
+__host__ __device__ inline int sl_bw(int lay) { return sl_col(lay) ? lay - kColLay : 1 << lay; }
+__host__ __device__ inline int sl_bh(int lay) {
+  return sl_col(lay) ? (kThreads / (lay - kColLay)) & ~15 : kThreads >> lay;
+}
+__host__ __device__ inline int sl_tw(int lay) { return 4 * sl_bw(lay); }
+__host__ __device__ inline int sl_th(int lay) { return 2 * sl_bh(lay); }
+// staged row stride in float2 slots (room for the skew) and the skew (r >> ks) & km of a layout
+__host__ __device__ inline int sl_sw2(int lay, int rx) {
+  const int w = sl_tw(lay) + 2 * rx;
+  return sl_col(lay) ? ((w + 1) | 1) : (w + 3 + 7) & ~7;
+}
+__host__ __device__ inline int sl_skew_shift(int lay) { return sl_col(lay) ? 4 : 1; }
+__host__ __device__ inline int sl_skew_mask(int lay) { return sl_col(lay) ? 1 : 3; }
+__device__ __forceinline__ int sl_index(int r, int c, int sw2, int ks, int km) { return r * sw2 + c + ((r >> ks) & km); }
 constexpr int kSlQ = 6 * 4;  // missing-point moments per thread: [k][g], both rows in one int32
 
 // Tensor maps of the elevation for the TMA staging, one per tile layout (index stage_map()).
+constexpr int kStageMaps = 5;
 struct StageMaps {
-  CUtensorMap map[3];
+  CUtensorMap map[kStageMaps];
 };
-__host__ __device__ inline int stage_map(int lay) { return lay == 2 ? 0 : (lay == 3 ? 1 : 2); }
+__host__ __device__ inline int stage_map(int lay) {
+  return lay == 2 ? 0 : lay == 3 ? 1 : lay == 5 ? 2 : lay == kColLay + 3 ? 3 : 4;
+}
 // Width of the TMA box of a layout: the staged width plus the slack of rounding the box's first
 // column down to a multiple of q = 16 bytes / element size, rounded up to a multiple of q.
 __host__ __device__ inline int stage_box_w(int lay, int rx, int q) {
@@ -514,17 +535,18 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int ty0 = R.ty + (t / L.tiles_x[ri]) * th;
   const int rx = T.rx, ry = T.ry;
   const int sw = tw + 2 * rx, sh = th + 2 * ry, sw2 = sl_sw2(lay, rx);
+  const int ks = sl_skew_shift(lay), km = sl_skew_mask(lay);
   const int tid = threadIdx.x;
 
   const float qnan = __int_as_float(0x7fc00000);
   // Each staged value v goes to two vertical pairs: (row, row + 1).x and (row - 1, row).y.
   auto put = [&](int row, int col, float v) {
     if (!SEB_IN_BOUNDS(L.err, row >= 0 && row < sh && row < kMaxStageRows && col >= 0 && col < sw &&
-                                  (row < sh - 1 ? sl_index(row, col, sw2) : sl_index(row - 1, col, sw2)) < L.pairs_alloc))
+                                  (row < sh - 1 ? sl_index(row, col, sw2, ks, km) : sl_index(row - 1, col, sw2, ks, km)) < L.pairs_alloc))
       return;
     if (v != v) rowflag[row] = 1;
-    if (row < sh - 1) pt[sl_index(row, col, sw2)].x = v;
-    if (row > 0) pt[sl_index(row - 1, col, sw2)].y = v;
+    if (row < sh - 1) pt[sl_index(row, col, sw2, ks, km)].x = v;
+    if (row > 0) pt[sl_index(row - 1, col, sw2, ks, km)].y = v;
   };
   const int dr = kThreads / sw, dc = kThreads - dr * sw;  // row-major walk in steps of kThreads cells
   if (L.tma) {
@@ -592,13 +614,28 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
   }
 
-  // block (cb, rp) of this thread: a half-warp holds 4 blocks x 4 pair rows
-  const int cbs = 1 << lay, c4 = cbs >> 2;
-  const int cb = (tid & 3) + 4 * ((tid >> 4) % c4);
-  const int rp = ((tid >> 2) & 3) + 4 * ((tid >> 4) / c4);
+  // block (cb, rp) of this thread: a half-warp holds 4 blocks x 4 pair rows (quad layouts) or one
+  // block column x 16 block rows (column layouts; threads past W x H idle on a copy of a block)
+  int cb, rp;
+  bool idle = false;
+  if (sl_col(lay)) {
+    const int bh = sl_bh(lay), bw = sl_bw(lay);
+    cb = tid / bh;
+    rp = tid - cb * bh;
+    if (cb >= bw) {
+      cb = bw - 1;
+      idle = true;
+    }
+  } else {
+    const int c4 = (1 << lay) >> 2;
+    cb = (tid & 3) + 4 * ((tid >> 4) % c4);
+    rp = ((tid >> 2) & 3) + 4 * ((tid >> 4) / c4);
+  }
   const int lx = 4 * cb, ly = 2 * rp;
   const int cx = tx0 + lx, cy = ty0 + ly;
-  auto stores = [&](int c, int r) { return c >= R.x0 && c < R.x0 + R.w && r >= R.y0 && r < R.y0 + R.h; };
+  auto stores = [&](int c, int r) {
+    return !idle && c >= R.x0 && c < R.x0 + R.w && r >= R.y0 && r < R.y0 + R.h;
+  };
   {
     // a warp without a cell to store (outside the rectangle, or masked out) skips the work;
     // no block-wide barrier follows
@@ -611,7 +648,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int pair = blockIdx.y;
   const int r0 = T.run_start[pair], r1 = T.run_start[pair + 1];
   auto tile_at = [&](int row, int col) {
-    return row < sh - 1 ? pt[sl_index(row, col, sw2)].x : pt[sl_index(row - 1, col, sw2)].y;
+    return row < sh - 1 ? pt[sl_index(row, col, sw2, ks, km)].x : pt[sl_index(row - 1, col, sw2, ks, km)].y;
   };
   // block reference: first known cell of the block (rows outer), else of the footprint of
   // its first cell in run order, else 0 (then every cell of the block is unknown)
@@ -674,10 +711,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     // free: band tiles of a rolling shift touch the window edge, where nearly every run holds an
     // unknown cell, and there the per-run vote costs more than it saves.
     const bool masked = L.all_masked || __any_sync(0xffffffffu, rowflag[row] | rowflag[row + 1]);
-    const float2* pq = pt + sl_index(row, rx + lx + lo, sw2);  // pq[k]: column lo + k of the block
+    const float2* pq = pt + sl_index(row, rx + lx + lo, sw2, ks, km);  // pq[k]: column lo + k of the block
     const int len = hi - lo + 1;
     if (!SEB_IN_BOUNDS(L.err, row >= 0 && row + 1 < sh && rx + lx + lo >= 0 && rx + lx + hi + 3 < sw &&
-                                  sl_index(row, rx + lx + hi + 3, sw2) < L.pairs_alloc))
+                                  sl_index(row, rx + lx + hi + 3, sw2, ks, km) < L.pairs_alloc))
       continue;
     const float flo = (float)lo, fhi = (float)hi;
     const float2 dj2 = f2((float)dj, (float)dj);
@@ -984,7 +1021,22 @@ void decompose_sl(Launch& L) {
       push(ax + Wm, ay, ax + Wm, q.y0, x1, y1, 2);
       push(ax, ay + Hm, q.x0, ay + Hm, ax + Wm, y1, 5);
     } else if (W < H) {
-      push(ax, ay, q.x0, q.y0, x1, y1, 2);
+      // a column band: tiles exactly as wide as the band where it is 3 or 5 blocks wide (a band
+      // of up to 8 blocks is cut into at most two such pieces and 4-block ones), layout 2
+      // otherwise (at most 3 rectangles per requested one, so kMaxRects holds 4 of them)
+      int nb = (W + 3) / 4, x = ax;
+      if (nb > 8) {
+        push(ax, ay, q.x0, q.y0, x1, y1, 2);
+        nb = 0;
+      }
+      while (nb > 0) {
+        const int t = nb <= 5 ? nb : (nb - 3 < 5 ? nb - 3 : 5);
+        const int lay = t == 3 ? kColLay + 3 : (t == 5 ? kColLay + 5 : 2);
+        const int xe = x + 4 * t < x1 ? x + 4 * t : x1;
+        push(x, ay, x > q.x0 ? x : q.x0, q.y0, xe, y1, lay);
+        x += 4 * t;
+        nb -= t;
+      }
     } else {
       push(ax, ay, q.x0, q.y0, x1, y1, 5);
     }
@@ -1040,10 +1092,10 @@ bool stage_maps(const Tables& T, const Launch& L, StageMaps* M) {
                                          : (sizeof(E) == 2 && std::is_same<E, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                                                              : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
   memset(M, 0, sizeof(*M));
-  bool used[3] = {false, false, false};
+  bool used[kStageMaps] = {false, false, false, false, false};
   for (int i = 0; i < L.n_rects; ++i) used[stage_map(L.rects[i].log_tpr)] = true;
-  const int lays[3] = {2, 3, 5};
-  for (int m = 0; m < 3; ++m) {
+  const int lays[kStageMaps] = {2, 3, 5, kColLay + 3, kColLay + 5};
+  for (int m = 0; m < kStageMaps; ++m) {
     if (!used[m]) continue;
     const int lay = lays[m];
     const int bw = stage_box_w(lay, T.rx, q), bh = sl_th(lay) + 2 * T.ry;
