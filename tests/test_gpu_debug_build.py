@@ -1,8 +1,10 @@
 """The bounds-checked build (libseb_debug.so, compiled with -DSEB_DEBUG): every index of the
 staged tile, of the row runs and of the output stores is checked in the kernel, and a failed
 check raises a bit of the device error word instead of touching memory.  A child process runs
-the map paths on it (rebuild and rolling shifts with the TMA staging, a ragged map with plain
-loads, the compensated sums and the tiled BF16 storage); seb_map_check must find the error word
+the map paths on it (rebuild and rolling shifts with the TMA staging, shifts whose column bands
+take the column layouts, a ragged map with plain loads, the compensated sums, the tiled BF16
+storage, and a footprint whose packed missing-point moments are flushed); seb_map_check must find
+the error word
 clear, and the outputs must equal the release build's bit for bit."""
 import os
 import subprocess
@@ -55,6 +57,22 @@ m.check()
 m = seb.SebMap(seb.SebParams(nx=n, ny=n, elev_dtype="bf16_tiled", **C2))
 m.update(seb.encode_bf16_tiled(e), (0, 0))
 res["tiled"] = m.outputs()[0].cpu().numpy()
+m.check()
+# moves whose column bands are 3, 4 and 5 blocks wide (column layouts, piece cutting)
+m = seb.SebMap(seb.SebParams(nx=n, ny=n, **C2))
+o = [130, 130]
+m.update(win(o), tuple(o))
+for dx, dy in [(2, 0), (10, 1), (-6, 0), (-13, 2), (17, -3)]:
+    o = [o[0] + dx, o[1] + dy]
+    m.shift(win(o), tuple(o))
+res["bands"] = m.outputs()[0].cpu().numpy()
+m.check()
+# a footprint whose missing-point moments are flushed from the packed words every few runs
+F = dict(n_yaw=4, res=0.05, length=1.3, width=0.9)
+m = seb.SebMap(seb.SebParams(nx=96, ny=72, **F))
+m.update(world[100:172, 100:196].contiguous(), (100, 100))
+m.shift(world[97:169, 104:200].contiguous(), (104, 97))
+res["flushed"] = m.outputs()[0].cpu().numpy()
 m.check()
 np.savez(sys.argv[2], **res)
 print("library", seb.abi.LIB_PATH)
