@@ -764,14 +764,15 @@ __global__ void __launch_bounds__(kThreads, 2)
       for (int t = 0; t < 3; ++t) slide(t, add2(pq[t], nref), add2(pq[len + t], nref));
     } else {
       // unknown heights: z' = 0 (the known ones get exactly the plain path's z - ref); the packed
-      // word u = [x unknown] + 65536 [y unknown] counts them for both rows at once
+      // word u = [x unknown] + 65536 [y unknown] counts them for both rows at once.  The NaN tests
+      // give all-ones / zero masks, so z' and the counts are bitwise ANDs, not selects.
       constexpr int kP = 0x10001;
       auto zof = [&](int k, float2& zp, int& u) {
         const float2 v = pq[k];
-        const bool kx = v.x == v.x, ky = v.y == v.y;
+        const uint32_t mx = 0u - (uint32_t)(v.x == v.x), my = 0u - (uint32_t)(v.y == v.y);
         const float2 zr = add2(v, nref);
-        zp = f2(kx ? zr.x : 0.f, ky ? zr.y : 0.f);
-        u = (kx ? 0 : 1) + (ky ? 0 : 0x10000);
+        zp = f2(__uint_as_float(__float_as_uint(zr.x) & mx), __uint_as_float(__float_as_uint(zr.y) & my));
+        u = (int)((~mx & 1u) | (~my & 0x10000u));
       };
       // Known weights summed three times over (k1 = sum m, k2 = sum (len - k) m_k,
       // k3 = sum (len - k)(len - k + 1) / 2 m_k, packed like Qp); with u = len - k the missing
@@ -783,13 +784,13 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll 2
       for (int k = 0; k < len; ++k) {
         const float2 v = pq[k];
-        const bool kx = v.x == v.x, ky = v.y == v.y;
+        const uint32_t mx = 0u - (uint32_t)(v.x == v.x), my = 0u - (uint32_t)(v.y == v.y);
         const float2 zr = add2(v, nref);
-        const float2 zp = f2(kx ? zr.x : 0.f, ky ? zr.y : 0.f);
+        const float2 zp = f2(__uint_as_float(__float_as_uint(zr.x) & mx), __uint_as_float(__float_as_uint(zr.y) & my));
         Ab = add2(Ab, zp);
         Tb = add2(Tb, Ab);
         Cb = fma2(zp, zp, Cb);
-        k1 += (kx ? 1 : 0) + (ky ? 0x10000 : 0);
+        k1 += (int)((mx & 1u) | (my & 0x10000u));
         k2 += k1;
         k3 += k2;
       }
