@@ -512,18 +512,17 @@ __global__ void init_kernel(float* __restrict__ p, float* __restrict__ m, float*
 }
 
 // ------------------------------------------------------------------------------------------------
-// Tensor-core convolution (tcgen05, sm_100 family): the 32 -> 32 dilated 3x3 layers as an
-// implicit GEMM D[128 pixels][32] = A[128][288] B[288][32], A the im2col rows of 128 output
-// pixels and B the weights, both BF16 and K-major in shared memory in the canonical layout
-// without swizzle (core matrices of 8 rows x 16 bytes; K-adjacent core matrices LBO bytes
-// apart, M/N-adjacent ones SBO bytes apart), FP32 accumulation in tensor memory.
+// Tensor-core convolution (tcgen05, sm_100 family): the 32 -> 32 dilated 3x3 layers as implicit
+// GEMMs D[128 pixels][32] = A[128][288] B[288][32] (K = 9 taps x 32 channels), both operands BF16
+// and K-major in shared memory in the canonical layout without swizzle (core matrices of 8 rows x
+// 16 bytes; K-adjacent core matrices LBO bytes apart, M/N-adjacent ones SBO bytes apart), FP32
+// accumulation in tensor memory.
 // ------------------------------------------------------------------------------------------------
 constexpr int kTcM = 128;
 constexpr int kTcK = 9 * kHid;                      // 288
 constexpr int kTcKCores = kTcK / 8;                  // 36
 constexpr int kTcBOff = 72 * 1024;                   // B right after A (128 x 288 BF16), 1 KB aligned
 constexpr int kTcBarOff = kTcBOff + 18 * 1024;       // after B (32 x 288 BF16)
-constexpr int kTcSmem = kTcBarOff + 256;             // + barrier: two CTAs fit on an SM
 static_assert(kTcBOff >= kTcM * kTcK * 2 && kTcBarOff >= kTcBOff + kHid * kTcK * 2, "operand regions overlap");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -546,138 +545,15 @@ __device__ __forceinline__ uint32_t tc_off(int row, int k, int nrow_cores) {
   return (uint32_t)((((k >> 3) * nrow_cores + (row >> 3)) * 128) + (row & 7) * 16 + (k & 7) * 2);
 }
 
-template <bool RELU>
-__global__ void __launch_bounds__(kTcM, 2) conv_tc_kernel(const bf16* __restrict__ x, const bf16* __restrict__ w,
-                                                          const float* __restrict__ bias, int B, int H, int W, int d,
-                                                          bf16* __restrict__ y, uint32_t* err) {
-  extern __shared__ __align__(1024) uint8_t tsm[];
-  uint8_t* As = tsm;
-  uint8_t* Bs = tsm + kTcBOff;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(tsm + kTcBarOff);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(tsm + kTcBarOff + 16);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int Ho = H - 2 * d, Wo = W - 2 * d;
-  const int64_t P = (int64_t)B * Ho * Wo;
-  const int64_t p = (int64_t)blockIdx.x * kTcM + tid;
-
-  // Operands are copied global -> shared with cp.async (16 bytes each, all in flight at once).
-  auto cp16 = [](uint8_t* dst, const void* src, uint32_t bytes) {  // bytes < 16: zero fill
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(bytes)
-                 : "memory");
-  };
-  // B: weights [co][tap][ci] -> K-major rows co, k = tap * 32 + ci
-  for (int i = tid; i < kHid * kTcKCores; i += kTcM) {
-    const int co = i / kTcKCores, kc = i - co * kTcKCores;
-    cp16(Bs + tc_off(co, kc * 8, kHid / 8), w + (int64_t)co * kTcK + kc * 8, 16u);
-  }
-  // A: this thread's im2col row (zeros past the last pixel)
-  {
-    int b = 0, i = 0, j = 0;
-    const uint32_t bytes = p < P ? 16u : 0u;
-    if (p < P) {
-      b = (int)(p / ((int64_t)Ho * Wo));
-      const int rem = (int)(p - (int64_t)b * Ho * Wo);
-      i = rem / Wo;
-      j = rem - i * Wo;
-    }
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int u = tap / 3, v = tap - u * 3;
-      const bf16* src = x + (((int64_t)b * H + i + u * d) * W + j + v * d) * kHid;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) cp16(As + tc_off(tid, tap * kHid + q * 8, kTcM / 8), src + q * 8, bytes);
-    }
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)), "r"(32));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands visible to the tensor core
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *tslot;
-  if (tid == 0) {
-    const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
-    // K step of 16 = two K core matrices
-    const uint32_t a_lbo = (kTcM / 8) * 128, a_sbo = 128, b_lbo = (kHid / 8) * 128, b_sbo = 128;
-    for (int s = 0; s < kTcK / 16; ++s) {
-      const uint64_t ad = tc_desc(a0 + s * 2 * a_lbo, a_lbo, a_sbo);
-      const uint64_t bd = tc_desc(b0 + s * 2 * b_lbo, b_lbo, b_sbo);
-      const uint32_t acc = s > 0 ? 1u : 0u;
-      asm volatile(
-          "{\n .reg .pred pa;\n setp.ne.b32 pa, %4, 0;\n"
-          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}" ::"r"(tmem),
-          "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(acc));
-    }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
-                 : "memory");
-  }
-  // bounded wait for the MMAs
-  uint32_t done = 0;
-  for (int it = 0; it < (1 << 20) && !done; ++it) {
-    asm volatile(
-        "{\n .reg .pred pw;\n mbarrier.try_wait.parity.shared::cta.b64 pw, [%1], %2;\n selp.u32 %0, 1, 0, pw;\n}"
-        : "=r"(done)
-        : "r"(smem_u32(mbar)), "r"(0)
-        : "memory");
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!done) {
-    if (tid == 0) atomicOr(err, 4u);
-  } else {
-    uint32_t r[32];
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    if (p < P) {
-      // 16-byte stores: the 32 outputs of a pixel are 64 contiguous bytes
-      uint4* yp = reinterpret_cast<uint4*>(y + p * kHid);
-#pragma unroll
-      for (int q = 0; q < kHid / 8; ++q) {
-        uint4 v;
-        __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(&v);
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int o = 8 * q + 2 * t;
-          float v0 = __uint_as_float(r[o]) + bias[o], v1 = __uint_as_float(r[o + 1]) + bias[o + 1];
-          if (RELU) {
-            v0 = fmaxf(v0, 0.f);
-            v1 = fmaxf(v1, 0.f);
-          }
-          h2[t] = __floats2bfloat162_rn(v0, v1);
-        }
-        yp[q] = v;
-      }
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 0) {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32));
-  }
-}
-
 // ------------------------------------------------------------------------------------------------
 // Tensor-core backward of the 32 -> 32 layers (tcgen05, the same operand layout and instruction
-// descriptor as conv_tc_kernel: BF16, K-major, no swizzle, M = 128, N = 32, FP32 in tensor memory).
+// descriptor as the forward: BF16, K-major, no swizzle, M = 128, N = 32, FP32 in tensor memory).
 // The FP32 gradient dz = dy * (y > 0) enters as two BF16 operands, hi = bf16(dz) and
 // lo = bf16(dz - hi), multiplied by the same BF16 weights or activations and accumulated in FP32:
 // every product is exact and hi + lo carries dz to about 2^-17, so the tensor-core gradients
 // track the FP32 CUDA-core ones.
 // ------------------------------------------------------------------------------------------------
-struct TcSync {  // one-thread MMA issue, commit and a bounded wait, as in conv_tc_kernel
+struct TcSync {  // one-thread MMA issue, commit and a bounded wait
   uint64_t* bar;
   __device__ void issue(uint32_t tmem_d, uint32_t a0, uint32_t a_lbo, uint32_t b0, uint32_t b_lbo, int ksteps,
                         bool acc_first) const {
@@ -747,6 +623,124 @@ __device__ __forceinline__ uint4 pack8(const float v[8]) {
 #pragma unroll
   for (int t = 0; t < 4; ++t) h[t] = __floats2bfloat162_rn(v[2 * t], v[2 * t + 1]);
   return o;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Tensor-core forward of the 32 -> 32 layers as an implicit GEMM over a 2-D tile of R x C output
+// pixels of one image.  The tile's input window, R + 2d rows of Pt = C + 2d pixels (zero outside
+// the image), is staged once, as 4 channel groups of [pixel][8 channels] rows of 16 bytes.  Output
+// pixel (r, c) of the tile is GEMM row m = r Pt + c (rows with c >= C are computed and dropped),
+// and tap (u, v) reads staged pixel m + u d Pt + v d: the A operand of a tap is the staged window
+// itself, started that many rows later, so only the descriptor's start address changes from tap
+// to tap (16 bytes per pixel) and no pixel is copied per tap.  K-adjacent core matrices are the
+// next channel group (LBO = S x 16 bytes), M-adjacent ones the next 8 pixels (SBO = 128).  Up to 4
+// M tiles of 128 rows accumulate in 4 x 32 TMEM columns.
+// ------------------------------------------------------------------------------------------------
+struct ConvTile {
+  int C, R, Pt, mt, S;  // tile columns and rows, window pitch, M tiles, staged pixels
+};
+constexpr int kCtMaxS = 1328;                       // staged pixels: 4 x 16 bytes each (83 KB)
+constexpr int kCtBOff = kCtMaxS * 64;               // weights (32 x 288 BF16) after the window
+constexpr int kCtBarOff = kCtBOff + 18 * 1024;
+constexpr int kCtSmem = kCtBarOff + 64;             // + barrier and TMEM slot: two CTAs per SM
+static_assert(kCtBOff % 1024 == 0, "weights 1 KB aligned");
+
+template <bool RELU>
+__global__ void __launch_bounds__(kTcM, 2) conv_tc_tile_kernel(const bf16* __restrict__ x, const bf16* __restrict__ w,
+                                                               const float* __restrict__ bias, int H, int W, int d,
+                                                               ConvTile T, int tiles_x, int tiles_y,
+                                                               bf16* __restrict__ y, uint32_t* err) {
+  extern __shared__ __align__(1024) uint8_t tsm[];
+  uint8_t* As = tsm;
+  uint8_t* Bs = tsm + kCtBOff;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(tsm + kCtBarOff);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tsm + kCtBarOff + 16);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int Ho = H - 2 * d, Wo = W - 2 * d;
+  if (blockDim.x != kTcM || T.S > kCtMaxS || T.mt < 1 || T.mt > 4) {
+    if (tid == 0) atomicOr(err, 4u);
+    return;
+  }
+  int t = blockIdx.x;
+  const int tx = t % tiles_x;
+  t /= tiles_x;
+  const int ty = t % tiles_y, b = t / tiles_y;
+  const int i0 = ty * T.R, j0 = tx * T.C;
+
+  auto cp16 = [](uint8_t* dst, const void* src, uint32_t bytes) {  // bytes 0: zero fill
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(bytes)
+                 : "memory");
+  };
+  // B: weights [co][tap][ci] -> K-major rows co, k = tap * 32 + ci
+  for (int i = tid; i < kHid * kTcKCores; i += kTcM) {
+    const int co = i / kTcKCores, kc = i - co * kTcKCores;
+    cp16(Bs + tc_off(co, kc * 8, kHid / 8), w + (int64_t)co * kTcK + kc * 8, 16u);
+  }
+  // A: staged pixel s = rr * Pt + cc of the window, channel group g at (g * S + s) * 16 bytes;
+  // four consecutive threads copy one pixel's 64 bytes
+  const int rows = T.R + 2 * d;
+  for (int e = tid; e < T.S * 4; e += kTcM) {
+    const int s = e >> 2, g = e & 3;
+    const int rr = s / T.Pt, cc = s - rr * T.Pt;
+    const int gi = i0 + rr, gj = j0 + cc;
+    const bool in = rr < rows && gi < H && gj < W;
+    const bf16* src = in ? x + (((int64_t)b * H + gi) * W + gj) * kHid + g * 8 : x;
+    cp16(As + ((size_t)g * T.S + s) * 16, src, in ? 16u : 0u);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands visible to the tensor core
+  const uint32_t tmem = tmem_alloc_cols(tslot, warp, 128);    // (its barrier publishes the copies)
+  const TcSync sync{mbar};
+  if (tid == 0) {
+    const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+    const uint32_t a_lbo = (uint32_t)T.S * 16u, b_lbo = (kHid / 8) * 128;
+    for (int m = 0; m < T.mt; ++m) {
+      for (int s = 0; s < kTcK / 16; ++s) {
+        const int tap = s >> 1, u = tap / 3, v = tap - 3 * (tap / 3);
+        const uint32_t row = (uint32_t)(m * kTcM + u * d * T.Pt + v * d);
+        const uint64_t ad = tc_desc(a0 + (uint32_t)(s & 1) * 2u * a_lbo + row * 16u, a_lbo, 128);
+        const uint64_t bd = tc_desc(b0 + s * 2 * b_lbo, b_lbo, 128);
+        const uint32_t acc = s > 0 ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred pa;\n setp.ne.b32 pa, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}" ::"r"(tmem + (uint32_t)(m * kHid)),
+            "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(acc));
+      }
+    }
+    sync.commit();
+  }
+  if (!sync.wait(0)) {
+    // the MMAs did not finish in time: report it, give them one more bounded wait (they write
+    // this CTA's tensor memory) and leave the tile unwritten
+    if (tid == 0) {
+      atomicOr(err, 4u);
+      sync.wait(0);
+    }
+  } else {
+    for (int m = 0; m < T.mt; ++m) {
+      uint32_t r[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(m * kHid), r);
+      const int row = m * kTcM + tid, rr = row / T.Pt, cc = row - rr * T.Pt;
+      const int gi = i0 + rr, gj = j0 + cc;
+      if (rr < T.R && cc < T.C && gi < Ho && gj < Wo) {
+        // 16-byte stores: the 32 outputs of a pixel are 64 contiguous bytes
+        uint4* yp = reinterpret_cast<uint4*>(y + (((int64_t)b * Ho + gi) * Wo + gj) * kHid);
+#pragma unroll
+        for (int q = 0; q < kHid / 8; ++q) {
+          float v[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const float a = __uint_as_float(r[8 * q + e]) + bias[8 * q + e];
+            v[e] = RELU ? fmaxf(a, 0.f) : a;
+          }
+          yp[q] = pack8(v);
+        }
+      }
+    }
+  }
+  tmem_free_cols(tmem, warp, 128);
 }
 
 // Input side: dx[p][c] = sum_{tap, o} dz[p - tap offset][o] w[o][tap][c] as the implicit GEMM
@@ -1383,6 +1377,30 @@ int seb_sur_gather(seb_sur* h, const float* elev, const float* exact, int32_t nx
   return cuda_check(cudaGetLastError(), "gather launch");
 }
 
+// Tile of conv_tc_tile_kernel for dilation d and an Ho x Wo output: the column count C (a
+// multiple of 8 up to 64, or all of Wo) and the row count R (up to 4 M tiles of 128 rows, the
+// window within kCtMaxS pixels) that stage the fewest pixels for the whole output.
+static ConvTile conv_tile(int d, int Ho, int Wo) {
+  ConvTile best{0, 0, 0, 0, 0};
+  double best_score = 1e300;
+  for (int c = 8; c <= 64 + 7; c += 8) {
+    const int C = c < Wo ? c : Wo;
+    const int Pt = C + 2 * d;
+    int R = (4 * kTcM) / Pt < Ho ? (4 * kTcM) / Pt : Ho;
+    auto staged = [&](int r) { return (r * Pt + kTcM - 1) / kTcM * kTcM + 2 * d * Pt + 2 * d; };
+    while (R > 0 && staged(R) > kCtMaxS) --R;
+    if (R > 0) {
+      const double score = (double)((Wo + C - 1) / C) * ((Ho + R - 1) / R) * staged(R);
+      if (score < best_score) {
+        best_score = score;
+        best = ConvTile{C, R, Pt, (R * Pt + kTcM - 1) / kTcM, staged(R)};
+      }
+    }
+    if (C == Wo) break;
+  }
+  return best;
+}
+
 // One 3x3 layer l (0..3) on x [B][S][S'][Cin] -> y; the 32 -> 32 layers use the tensor-core
 // kernel when the handle's engine says so.
 static void conv_layer(seb_sur* h, const bf16* x, int l, int B, int H, int W, bf16* y) {
@@ -1393,9 +1411,12 @@ static void conv_layer(seb_sur* h, const bf16* x, int l, int B, int H, int W, bf
     conv_fwd_kernel<kInF><<<grid_for(pix, 128), 128, 0, h->stream>>>(x, wb + h->PL.w[0], master + h->PL.b[0], B, H,
                                                                       W, kDil[0], y);
   } else if (h->engine == SEB_SUR_TCGEN05) {
-    cudaFuncSetAttribute(conv_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-    conv_tc_kernel<true><<<(unsigned)((pix + kTcM - 1) / kTcM), kTcM, kTcSmem, h->stream>>>(
-        x, wb + h->PL.w[l], master + h->PL.b[l], B, H, W, kDil[l], y, h->err);
+    const int d = kDil[l], Ho = H - 2 * d, Wo = W - 2 * d;
+    const ConvTile T = conv_tile(d, Ho, Wo);
+    const int tx = (Wo + T.C - 1) / T.C, ty = (Ho + T.R - 1) / T.R;
+    cudaFuncSetAttribute(conv_tc_tile_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCtSmem);
+    conv_tc_tile_kernel<true><<<(unsigned)((int64_t)B * ty * tx), kTcM, kCtSmem, h->stream>>>(
+        x, wb + h->PL.w[l], master + h->PL.b[l], H, W, d, T, tx, ty, y, h->err);
   } else {
     conv_fwd_kernel<kHid><<<grid_for(pix, 128), 128, 0, h->stream>>>(x, wb + h->PL.w[l], master + h->PL.b[l], B, H,
                                                                       W, kDil[l], y);
