@@ -743,14 +743,6 @@ __global__ void __launch_bounds__(kTcM, 2) conv_tc_tile_kernel(const bf16* __res
   tmem_free_cols(tmem, warp, 128);
 }
 
-// Input side: dx[p][c] = sum_{tap, o} dz[p - tap offset][o] w[o][tap][c] as the implicit GEMM
-// D[128 input pixels][32 c] = A[128][288] B[288][32], A the rows (tap, o) of dz (0 outside the
-// output), B[k = tap * 32 + o][c] = w[o][tap][c]; once with dz's hi part, then accumulated with
-// its lo part.  Writes dx FP32 [B][H][W][32].
-constexpr int kBdBOff = kTcBOff;                 // B after A (72 KB)
-constexpr int kBdBarOff = kBdBOff + 18 * 1024;
-constexpr int kBdSmem = kBdBarOff + 256;
-
 // dz = dy * (y > 0) split into BF16 hi = bf16(dz) and lo = bf16(dz - hi), written over dy in
 // place: pixel p's 128 bytes become [hi 0..31 | lo 0..31].  One thread per pixel.
 __global__ void split_dz_kernel(float* __restrict__ dy, const bf16* __restrict__ y, int64_t P) {
@@ -793,50 +785,56 @@ __global__ void transpose_w_kernel(const bf16* __restrict__ w, bf16* __restrict_
   wt[i] = w[((int64_t)o * 9 + tap) * kHid + c];
 }
 
-__global__ void __launch_bounds__(kTcM, 2) conv_bwd_dx_tc_kernel(const bf16* __restrict__ dzs,
-                                                                 const bf16* __restrict__ wt, int B, int H, int W, int d,
-                                                                 float* __restrict__ dx, uint32_t* err) {
+// Input side: dx[p][c] = sum_{tap, o} dz[p - tap offset][o] w[o][tap][c] as the implicit GEMM
+// D[128 input pixels][32 c] = A[128][288] B[288][32], A the rows (tap, o) of dz (0 outside the
+// output), B[k = tap * 32 + o][c] = w[o][tap][c]; once with dz's hi part, then accumulated with
+// its lo part.  Writes dx FP32 [B][H][W][32].  Over 2-D tiles, the forward's scheme run
+// backwards: dx at input pixel (i, j) sums dz[i - u d][j - v d] over the taps, so a tile of R x C input pixels stages the dz window of rows
+// i0 - 2d .. i0 + R - 1 and columns j0 - 2d .. j0 + C - 1 (zero outside the layer's output), and
+// tap (u, v) of GEMM row m = r Pt + c reads staged pixel m + (2 - u) d Pt + (2 - v) d.  The window
+// is staged twice, the hi then the lo half of the split gradient, into the same shared memory;
+// the lo MMAs accumulate onto the hi ones.
+__global__ void __launch_bounds__(kTcM, 2) conv_bwd_dx_tile_kernel(const bf16* __restrict__ dzs,
+                                                                   const bf16* __restrict__ wt, int H, int W, int d,
+                                                                   ConvTile T, int tiles_x, int tiles_y,
+                                                                   float* __restrict__ dx, uint32_t* err) {
   extern __shared__ __align__(1024) uint8_t tsm[];
   uint8_t* As = tsm;
-  uint8_t* Bs = tsm + kBdBOff;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(tsm + kBdBarOff);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(tsm + kBdBarOff + 16);
+  uint8_t* Bs = tsm + kCtBOff;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(tsm + kCtBarOff);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tsm + kCtBarOff + 16);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int Ho = H - 2 * d, Wo = W - 2 * d;
-  const int64_t P = (int64_t)B * H * W;
-  const int64_t p = (int64_t)blockIdx.x * kTcM + tid;
+  if (blockDim.x != kTcM || T.S > kCtMaxS || T.mt < 1 || T.mt > 4) {
+    if (tid == 0) atomicOr(err, 8u);
+    return;
+  }
+  int t = blockIdx.x;
+  const int tx = t % tiles_x;
+  t /= tiles_x;
+  const int ty = t % tiles_y, b = t / tiles_y;
+  const int i0 = ty * T.R, j0 = tx * T.C;
   // B: K-major rows c, k = tap * 32 + o; wt holds w transposed to [c][tap][o] (transpose_w_kernel)
   for (int i = tid; i < kHid * kTcKCores; i += kTcM) {
     const int c = i / kTcKCores, kc = i - c * kTcKCores;
     *reinterpret_cast<uint4*>(Bs + tc_off(c, kc * 8, kHid / 8)) =
         reinterpret_cast<const uint4*>(wt + (int64_t)c * kTcK)[kc];
   }
-  int b = 0, r = 0, s = 0;
-  if (p < P) {
-    b = (int)(p / ((int64_t)H * W));
-    const int rem = (int)(p - (int64_t)b * H * W);
-    r = rem / W;
-    s = rem - r * W;
-  }
   if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
-  const uint32_t tmem = tmem_alloc_cols(tslot, warp, 32);
+  const uint32_t tmem = tmem_alloc_cols(tslot, warp, 128);
   const TcSync sync{mbar};
+  const int rows = T.R + 2 * d;
   bool ok = true;
   for (int part = 0; part < 2 && ok; ++part) {  // 0: hi, 1: lo
-    // A: this thread's row, 9 taps x 32 o of the split gradient (hi or lo half of the output
-    // pixel's 128 bytes), 16-byte copies, zero-filled outside the output or past the last pixel
-#pragma unroll 1
-    for (int tap = 0; tap < 9; ++tap) {
-      const int u = tap / 3, v = tap - u * 3;
-      const int i = r - u * d, j = s - v * d;
-      const bool in = p < P && i >= 0 && i < Ho && j >= 0 && j < Wo;
-      const bf16* src = dzs + (in ? (((int64_t)b * Ho + i) * Wo + j) * 2 * kHid : 0) + part * kHid;
-#pragma unroll
-      for (int oc = 0; oc < 4; ++oc)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(As + tc_off(tid, tap * kHid + oc * 8,
-                                                                                                kTcM / 8))),
-                     "l"(src + oc * 8), "r"(in ? 16u : 0u)
-                     : "memory");
+    for (int e = tid; e < T.S * 4; e += kTcM) {
+      const int s = e >> 2, g = e & 3;
+      const int rr = s / T.Pt, cc = s - rr * T.Pt;
+      const int gi = i0 - 2 * d + rr, gj = j0 - 2 * d + cc;
+      const bool in = rr < rows && gi >= 0 && gi < Ho && gj >= 0 && gj < Wo;
+      const bf16* src = in ? dzs + (((int64_t)b * Ho + gi) * Wo + gj) * 2 * kHid + part * kHid + g * 8 : dzs;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(As + ((size_t)g * T.S + s) * 16)),
+                   "l"(src), "r"(in ? 16u : 0u)
+                   : "memory");
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
     asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -845,28 +843,46 @@ __global__ void __launch_bounds__(kTcM, 2) conv_bwd_dx_tc_kernel(const bf16* __r
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (tid == 0) {
-      sync.issue(tmem, smem_u32(As), (kTcM / 8) * 128, smem_u32(Bs), (kHid / 8) * 128, kTcK / 16, part > 0);
+      const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+      const uint32_t a_lbo = (uint32_t)T.S * 16u, b_lbo = (kHid / 8) * 128;
+      for (int m = 0; m < T.mt; ++m) {
+        for (int s = 0; s < kTcK / 16; ++s) {
+          const int tap = s >> 1, u = tap / 3, v = tap - 3 * (tap / 3);
+          const uint32_t row = (uint32_t)(m * kTcM + (2 - u) * d * T.Pt + (2 - v) * d);
+          const uint64_t ad = tc_desc(a0 + (uint32_t)(s & 1) * 2u * a_lbo + row * 16u, a_lbo, 128);
+          const uint64_t bd = tc_desc(b0 + s * 2 * b_lbo, b_lbo, 128);
+          const uint32_t acc = (s > 0 || part > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred pa;\n setp.ne.b32 pa, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}" ::"r"(tmem + (uint32_t)(m * kHid)),
+              "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(acc));
+        }
+      }
       sync.commit();
     }
     ok = sync.wait((uint32_t)part);
-    ok = __syncthreads_and(ok) != 0;  // the next part overwrites A only after the MMAs read it
+    ok = __syncthreads_and(ok) != 0;  // the next part overwrites the window only after the MMAs read it
   }
   if (!ok) {  // report, give the MMAs in flight one more bounded wait, then free the columns
     if (tid == 0) atomicOr(err, 8u);
     sync.wait(0);
     sync.wait(1);
   } else {
-    uint32_t rr[32];
-    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), rr);
-    if (p < P) {
-      float4* o4 = reinterpret_cast<float4*>(dx + p * kHid);
+    for (int m = 0; m < T.mt; ++m) {
+      uint32_t rr[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(m * kHid), rr);
+      const int row = m * kTcM + tid, r = row / T.Pt, c = row - r * T.Pt;
+      const int gi = i0 + r, gj = j0 + c;
+      if (r < T.R && c < T.C && gi < H && gj < W) {
+        float4* o4 = reinterpret_cast<float4*>(dx + (((int64_t)b * H + gi) * W + gj) * kHid);
 #pragma unroll
-      for (int q = 0; q < kHid / 4; ++q)
-        o4[q] = make_float4(__uint_as_float(rr[4 * q]), __uint_as_float(rr[4 * q + 1]), __uint_as_float(rr[4 * q + 2]),
-                            __uint_as_float(rr[4 * q + 3]));
+        for (int q = 0; q < kHid / 4; ++q)
+          o4[q] = make_float4(__uint_as_float(rr[4 * q]), __uint_as_float(rr[4 * q + 1]), __uint_as_float(rr[4 * q + 2]),
+                              __uint_as_float(rr[4 * q + 3]));
+      }
     }
   }
-  tmem_free_cols(tmem, warp, 32);
+  tmem_free_cols(tmem, warp, 128);
 }
 
 // Weight side: dw[o][tap][c] = sum_p dz[p][o] x[p + tap offset][c] and db[o] = sum_p dz[p][o] as
@@ -1505,9 +1521,11 @@ int seb_sur_train_step(seb_sur* h, int32_t B, float lr, int32_t step, float* los
       // the weight partials have been summed: their buffer holds the transposed weights now
       bf16* wt = reinterpret_cast<bf16*>(part);
       transpose_w_kernel<<<grid_for(kHid * kTcK, 256), 256, 0, st>>>(wb + h->PL.w[l], wt);
-      cudaFuncSetAttribute(conv_bwd_dx_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBdSmem);
-      conv_bwd_dx_tc_kernel<<<(unsigned)(((int64_t)B * S * S + kTcM - 1) / kTcM), kTcM, kBdSmem, st>>>(
-          dzs, wt, B, S, S, d, at<float>(h, h->v.dact[l - 1]), h->err);
+      const ConvTile T = conv_tile(d, S, S);
+      const int tx = (S + T.C - 1) / T.C, ty = (S + T.R - 1) / T.R;
+      cudaFuncSetAttribute(conv_bwd_dx_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCtSmem);
+      conv_bwd_dx_tile_kernel<<<(unsigned)((int64_t)B * ty * tx), kTcM, kCtSmem, st>>>(
+          dzs, wt, S, S, d, T, tx, ty, at<float>(h, h->v.dact[l - 1]), h->err);
     } else {
       const int E = kHid * 9 * kHid + kHid;
       conv_bwd_dw_kernel<kHid><<<ch, 256, 0, st>>>(dy, y, xin, B, S, S, d, part);
