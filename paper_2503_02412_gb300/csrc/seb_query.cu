@@ -25,6 +25,7 @@
 //   - dC = (1/N) sum (dP_i e_i^T + e_i dP_i^T), e_i = P_i - mean;
 //   - dP_i / d(x, y, theta): px = c i - s j, py = s i + c j (metres), so d px / d theta = -py,
 //     d py / d theta = px; z_i = bilinear(x + px, y + py) with its cell-wise gradient.
+#include <algorithm>
 #include <math.h>
 #include <string.h>
 
@@ -344,9 +345,8 @@ struct LatTap {
 };
 
 template <typename E>
-__device__ __forceinline__ void lattice_fetch(const QTab& Q, const QLaunch& L, int q, float xl, float yl, float c,
-                                              float s, LatTap& t) {
-  const E* __restrict__ elev = static_cast<const E*>(L.elev);
+__device__ __forceinline__ void lattice_fetch(const QTab& Q, const QLaunch& L, const E* __restrict__ elev, int q,
+                                              float xl, float yl, float c, float s, LatTap& t) {
   const float di = (float)Q.di[q], dj = (float)Q.dj[q];
   const float ox = c * di - s * dj, oy = s * di + c * dj;
   const float gxc = xl + ox, gyc = yl + oy;
@@ -380,7 +380,7 @@ template <typename E>
 __device__ __forceinline__ bool lattice_point(const QTab& Q, const QLaunch& L, int q, float xl, float yl, float c,
                                               float s, float& px, float& py, float& z, float& gx, float& gy) {
   LatTap t;
-  lattice_fetch<E>(Q, L, q, xl, yl, c, s, t);
+  lattice_fetch<E>(Q, L, static_cast<const E*>(L.elev), q, xl, yl, c, s, t);
   px = t.px;
   py = t.py;
   return lattice_eval(t, L, z, gx, gy);
@@ -394,8 +394,8 @@ constexpr int kQB = 4, kQBB = 2;
 // Moments of one pose by one thread, streaming its lattice in order (sums centred on the first
 // known point, as the grouped kernels do, but added in lattice order).
 template <typename E, int QB>
-__device__ __forceinline__ void stream_moments(const QTab& Q, const QLaunch& L, float xl, float yl, float c, float s,
-                                               float m[10], float& zref) {
+__device__ __forceinline__ void stream_moments(const QTab& Q, const QLaunch& L, const E* __restrict__ elev, float xl,
+                                               float yl, float c, float s, float m[10], float& zref) {
   for (int t = 0; t < 10; ++t) m[t] = 0.f;
   zref = 0.f;
   bool have = false;
@@ -404,7 +404,7 @@ __device__ __forceinline__ void stream_moments(const QTab& Q, const QLaunch& L, 
 #pragma unroll
     for (int u = 0; u < QB; ++u) {
       t[u].in = false;
-      if (q0 + u < Q.n) lattice_fetch<E>(Q, L, q0 + u, xl, yl, c, s, t[u]);
+      if (q0 + u < Q.n) lattice_fetch<E>(Q, L, elev, q0 + u, xl, yl, c, s, t[u]);
     }
 #pragma unroll
     for (int u = 0; u < QB; ++u) {
@@ -431,28 +431,21 @@ __device__ __forceinline__ void stream_moments(const QTab& Q, const QLaunch& L, 
 }
 
 // One pose per thread, for large batches: a warp then runs the eigen-solve, frame and adjoint
-// for 32 poses per pass (a group of GL lanes per pose runs them for 32 / GL).
+// for 32 poses per pass (a group of GL lanes per pose runs them for 32 / GL).  `elev` is the
+// window in global memory, or its copy in the CTA's shared memory.
 template <typename E>
-__global__ void __launch_bounds__(256) query_fwd1_kernel(const __grid_constant__ QTab Q,
-                                                         const __grid_constant__ QLaunch L) {
-  seb::pdl_entry();
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= L.n) return;
+__device__ __forceinline__ void fwd1_pose(const QTab& Q, const QLaunch& L, const E* __restrict__ elev, int64_t i) {
   float xl, yl, c, s;
   pose_local(L, L.poses + 3 * i, xl, yl, c, s);
   float m[10], zref;
-  stream_moments<E, kQB>(Q, L, xl, yl, c, s, m, zref);
+  stream_moments<E, kQB>(Q, L, elev, xl, yl, c, s, m, zref);
   QState S;
   finish_pose(Q, L, m, zref, c, s, S);
   store_pose(L, i, S);
 }
 
 template <typename E>
-__global__ void __launch_bounds__(256) query_bwd1_kernel(const __grid_constant__ QTab Q,
-                                                         const __grid_constant__ QLaunch L) {
-  seb::pdl_entry();
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= L.n) return;
+__device__ __forceinline__ void bwd1_pose(const QTab& Q, const QLaunch& L, const E* __restrict__ elev, int64_t i) {
   float xl, yl, c, s;
   pose_local(L, L.poses + 3 * i, xl, yl, c, s);
   QState S;
@@ -460,7 +453,7 @@ __global__ void __launch_bounds__(256) query_bwd1_kernel(const __grid_constant__
     load_pose(L, i, c, s, S);
   } else {
     float m[10], zref;
-    stream_moments<E, kQBB>(Q, L, xl, yl, c, s, m, zref);
+    stream_moments<E, kQBB>(Q, L, elev, xl, yl, c, s, m, zref);
     finish_pose(Q, L, m, zref, c, s, S);
   }
   float gpx = 0.f, gpy = 0.f, gth = 0.f;
@@ -473,7 +466,7 @@ __global__ void __launch_bounds__(256) query_bwd1_kernel(const __grid_constant__
 #pragma unroll
       for (int u = 0; u < kQBB; ++u) {
         t[u].in = false;
-        if (q0 + u < Q.n) lattice_fetch<E>(Q, L, q0 + u, xl, yl, c, s, t[u]);
+        if (q0 + u < Q.n) lattice_fetch<E>(Q, L, elev, q0 + u, xl, yl, c, s, t[u]);
       }
 #pragma unroll
       for (int u = 0; u < kQBB; ++u) {
@@ -494,6 +487,55 @@ __global__ void __launch_bounds__(256) query_bwd1_kernel(const __grid_constant__
   L.gpose[3 * i] = gpx;
   L.gpose[3 * i + 1] = gpy;
   L.gpose[3 * i + 2] = gth;
+}
+
+template <typename E>
+__global__ void __launch_bounds__(256) query_fwd1_kernel(const __grid_constant__ QTab Q,
+                                                         const __grid_constant__ QLaunch L) {
+  seb::pdl_entry();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.n) return;
+  fwd1_pose<E>(Q, L, static_cast<const E*>(L.elev), i);
+}
+
+template <typename E>
+__global__ void __launch_bounds__(256) query_bwd1_kernel(const __grid_constant__ QTab Q,
+                                                         const __grid_constant__ QLaunch L) {
+  seb::pdl_entry();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.n) return;
+  bwd1_pose<E>(Q, L, static_cast<const E*>(L.elev), i);
+}
+
+// The same with the whole window copied into the CTA's shared memory first: the ~140 bilinear
+// corner loads of a pose then come from shared memory instead of L1 / L2.  Persistent: each CTA
+// copies the window once and loops over poses.  It pays while three CTAs fit on an SM (a window
+// of up to kQMapSmem bytes: 100 x 100 FP32, or 180 x 180 BF16 at 0.1 m); with one CTA per SM
+// the lost occupancy costs more than the loads save, so larger windows stay in global memory.
+constexpr size_t kQMapSmem = 72 * 1024;
+template <typename E, bool BWD>
+__global__ void __launch_bounds__(256, 3) query1_smem_kernel(const __grid_constant__ QTab Q,
+                                                          const __grid_constant__ QLaunch L) {
+  extern __shared__ __align__(16) unsigned char qsm[];
+  E* map = reinterpret_cast<E*>(qsm);
+  seb::pdl_entry();
+  const E* g = static_cast<const E*>(L.elev);
+  const int64_t cells = (int64_t)L.nx * L.ny;
+  int64_t k0 = 0;
+  if (((uintptr_t)g & 15) == 0) {  // 16-byte copies, then the tail element by element
+    const int64_t n16 = cells * (int64_t)sizeof(E) / 16;
+    for (int64_t k = threadIdx.x; k < n16; k += blockDim.x)
+      reinterpret_cast<uint4*>(map)[k] = __ldg(reinterpret_cast<const uint4*>(g) + k);
+    k0 = n16 * 16 / (int64_t)sizeof(E);
+  }
+  for (int64_t k = k0 + threadIdx.x; k < cells; k += blockDim.x) map[k] = g[k];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (BWD)
+      bwd1_pose<E>(Q, L, map, i);
+    else
+      fwd1_pose<E>(Q, L, map, i);
+  }
 }
 
 template <typename E, int GL>
@@ -567,6 +609,21 @@ cudaError_t launch_q(const QTab& Q, const QLaunch& L, bool backward, cudaStream_
   if (L.n >= kOneLaneMin) {  // enough poses to fill the GPU with one pose per thread
     const int64_t blocks = (L.n + 255) / 256;
     if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+    const size_t map_bytes = (size_t)L.nx * L.ny * sizeof(E);
+    if (map_bytes <= kQMapSmem) {  // the window fits in shared memory: persistent CTAs
+      auto kern = backward ? query1_smem_kernel<E, true> : query1_smem_kernel<E, false>;
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)map_bytes);
+      int dev = 0, sms = 0, per_sm = 0;
+      if (e == cudaSuccess) e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, map_bytes);
+      if (e != cudaSuccess) return e;
+      if (per_sm > 0) {
+        const int64_t grid = std::min<int64_t>(blocks, (int64_t)sms * per_sm);
+        seb::launch_pdl(kern, dim3((unsigned)grid), dim3(256), map_bytes, st, Q, L);
+        return cudaGetLastError();
+      }
+    }
     if (backward)
       seb::launch_pdl(query_bwd1_kernel<E>, dim3((unsigned)blocks), dim3(256), 0, st, Q, L);
     else

@@ -224,17 +224,20 @@ def test_large_batch_and_empty(seb):
     compare(out.cpu().numpy()[idx], fl.cpu().numpy()[idx], r, rf, label="1M sample")
 
 
-def test_one_pose_per_thread_kernels(seb):
-    """Batches of 65,536 poses or more take the one-pose-per-thread kernels: their backward
-    against the FP64 oracle adjoint on a sample, the saved state against recomputation, and both
-    directions against the grouped kernels that the first 4,096 poses take when run alone (the
-    moment sums are added in a different order, so agreement is to FP32 rounding)."""
+@pytest.mark.parametrize("side", [100, 160])
+def test_one_pose_per_thread_kernels(seb, side):
+    """Batches of 65,536 poses or more take the one-pose-per-thread kernels (a 100 x 100 FP32
+    window, 40 KB, is copied into each CTA's shared memory; a 160 x 160 one, 100 KB, is read from
+    global memory): their backward against the FP64 oracle adjoint on a sample, the saved state
+    against recomputation, and both directions against the grouped kernels that the first 4,096
+    poses take when run alone (the moment sums are added in a different order, so agreement is to
+    FP32 rounding)."""
     from paper_2503_02412_gb300 import abi
 
-    cfg = dict(C1, kappa_max=1.0, phi_x_max=1.4, phi_y_max=1.4)
-    e = bumpy_plane(13)
+    cfg = dict(C1, nx=side, ny=side, kappa_max=1.0, phi_x_max=1.4, phi_y_max=1.4)
+    e = bumpy_plane(13, side, side)
     n = 70_000
-    poses = random_poses(14, n, 100, 100, 0.1, 5)
+    poses = random_poses(14, n, side, side, 0.1, 5)
     gout = np.random.default_rng(15).normal(size=(n, 5))
     g, out, fl = _bwd(seb, cfg, e, poses, gout)
     gs, outs, fls = _bwd(seb, cfg, e, poses[:4096], gout[:4096])
