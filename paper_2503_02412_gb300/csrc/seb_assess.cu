@@ -1064,6 +1064,8 @@ size_t smem_sl(const Tables& T, const Launch& L) {
   return kMaxStageRows * sizeof(float) + ((size_t)kSlQ * kThreads + pairs) * sizeof(float2) + 16;  // + mbarrier
 }
 
+}  // namespace
+
 // Driver entry point of cuTensorMapEncodeTiled (no link against libcuda), looked up once.
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -1079,6 +1081,8 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   });
   return fn;
 }
+
+namespace {
 
 // Tensor maps for the TMA staging of every layout in the launch; false (plain loads) when the
 // elevation's rows are not 16-byte multiples, a box exceeds 256 elements per side or the moment

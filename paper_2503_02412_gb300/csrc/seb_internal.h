@@ -1,6 +1,7 @@
 // Internal declarations shared by the libseb translation units (not part of the ABI).
 #pragma once
 
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
@@ -161,6 +162,9 @@ int query_setup(const seb_params& p, const void* elev, int64_t origin_i, int64_t
 cudaError_t launch_query(const QTab& Q, const QLaunch& L, int elev_dtype, bool backward, cudaStream_t st);
 
 // Kernel launchers (seb_assess.cu).
+// cuTensorMapEncodeTiled through the runtime's driver entry point (NULL when unavailable).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+
 cudaError_t launch_assess(const Tables& T, const Launch& L, int elev_dtype, int precision,
                           cudaStream_t stream);
 cudaError_t launch_copy_out(const Launch& L, float* out_dev, uint8_t* flags_dev,

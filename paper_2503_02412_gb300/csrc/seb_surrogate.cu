@@ -20,6 +20,7 @@
 
 #include <new>
 
+#include "seb_device.cuh"
 #include "seb_internal.h"
 
 namespace {
@@ -637,7 +638,8 @@ __device__ __forceinline__ uint4 pack8(const float v[8]) {
 // M tiles of 128 rows accumulate in 4 x 32 TMEM columns.
 // ------------------------------------------------------------------------------------------------
 struct ConvTile {
-  int C, R, Pt, mt, S;  // tile columns and rows, window pitch, M tiles, staged pixels
+  int C, R, Pt, mt, S;  // tile columns and rows, window pitch (C + 2d), M tiles, group stride in pixels
+                        // (Pt (R + 2d) rounded up to 8: each group's window starts 128-byte aligned)
 };
 constexpr int kCtMaxS = 1328;                       // staged pixels: 4 x 16 bytes each (83 KB)
 constexpr int kCtBOff = kCtMaxS * 64;               // weights (32 x 288 BF16) after the window
@@ -645,8 +647,12 @@ constexpr int kCtBarOff = kCtBOff + 18 * 1024;
 constexpr int kCtSmem = kCtBarOff + 64;             // + barrier and TMEM slot: two CTAs per SM
 static_assert(kCtBOff % 1024 == 0, "weights 1 KB aligned");
 
+// Window staging: with a tensor map (use_map), four TMA boxes {8 channels, Pt columns, R + 2d rows,
+// 1 image}, one per channel group, land in exactly the [group][pixel][16 bytes] layout above, zero
+// outside the image; otherwise 16-byte cp.async copies build the same layout.
 template <bool RELU>
-__global__ void __launch_bounds__(kTcM, 2) conv_tc_tile_kernel(const bf16* __restrict__ x, const bf16* __restrict__ w,
+__global__ void __launch_bounds__(kTcM, 2) conv_tc_tile_kernel(const __grid_constant__ CUtensorMap xmap, int use_map,
+                                                               const bf16* __restrict__ x, const bf16* __restrict__ w,
                                                                const float* __restrict__ bias, int H, int W, int d,
                                                                ConvTile T, int tiles_x, int tiles_y,
                                                                bf16* __restrict__ y, uint32_t* err) {
@@ -655,6 +661,7 @@ __global__ void __launch_bounds__(kTcM, 2) conv_tc_tile_kernel(const bf16* __res
   uint8_t* Bs = tsm + kCtBOff;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(tsm + kCtBarOff);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(tsm + kCtBarOff + 16);
+  uint64_t* tbar = reinterpret_cast<uint64_t*>(tsm + kCtBarOff + 32);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int Ho = H - 2 * d, Wo = W - 2 * d;
   if (blockDim.x != kTcM || T.S > kCtMaxS || T.mt < 1 || T.mt > 4) {
@@ -671,21 +678,27 @@ __global__ void __launch_bounds__(kTcM, 2) conv_tc_tile_kernel(const bf16* __res
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(bytes)
                  : "memory");
   };
+  if (use_map && tid == 0) {
+    seb::mbar_init(tbar, 1);
+    seb::mbar_arrive_expect_tx(tbar, (uint32_t)(T.Pt * (T.R + 2 * d)) * 64u);
+    for (int g = 0; g < 4; ++g) seb::tma_load_4d(As + (size_t)g * T.S * 16, &xmap, 8 * g, j0, i0, b, tbar);
+  }
   // B: weights [co][tap][ci] -> K-major rows co, k = tap * 32 + ci
   for (int i = tid; i < kHid * kTcKCores; i += kTcM) {
     const int co = i / kTcKCores, kc = i - co * kTcKCores;
     cp16(Bs + tc_off(co, kc * 8, kHid / 8), w + (int64_t)co * kTcK + kc * 8, 16u);
   }
-  // A: staged pixel s = rr * Pt + cc of the window, channel group g at (g * S + s) * 16 bytes;
-  // four consecutive threads copy one pixel's 64 bytes
-  const int rows = T.R + 2 * d;
-  for (int e = tid; e < T.S * 4; e += kTcM) {
-    const int s = e >> 2, g = e & 3;
-    const int rr = s / T.Pt, cc = s - rr * T.Pt;
-    const int gi = i0 + rr, gj = j0 + cc;
-    const bool in = rr < rows && gi < H && gj < W;
-    const bf16* src = in ? x + (((int64_t)b * H + gi) * W + gj) * kHid + g * 8 : x;
-    cp16(As + ((size_t)g * T.S + s) * 16, src, in ? 16u : 0u);
+  if (!use_map) {
+    // A: window pixel s = rr * Pt + cc, channel group g at (g * S + s) * 16 bytes; four
+    // consecutive threads copy one pixel's 64 bytes
+    for (int e = tid; e < T.S * 4; e += kTcM) {
+      const int s = e >> 2, g = e & 3;
+      const int rr = s / T.Pt, cc = s - rr * T.Pt;
+      const int gi = i0 + rr, gj = j0 + cc;
+      const bool in = gi < H && gj < W;
+      const bf16* src = in ? x + (((int64_t)b * H + gi) * W + gj) * kHid + g * 8 : x;
+      cp16(As + ((size_t)g * T.S + s) * 16, src, in ? 16u : 0u);
+    }
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
   asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -693,7 +706,16 @@ __global__ void __launch_bounds__(kTcM, 2) conv_tc_tile_kernel(const bf16* __res
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands visible to the tensor core
   const uint32_t tmem = tmem_alloc_cols(tslot, warp, 128);    // (its barrier publishes the copies)
   const TcSync sync{mbar};
-  if (tid == 0) {
+  // the window's TMA box has landed (bounded wait by the thread that issues the MMAs)
+  bool staged = true;
+  if (use_map && tid == 0) {
+    staged = seb::mbar_wait_bounded(tbar, 0, 1 << 20);
+    if (!staged) {
+      atomicOr(err, 4u);
+      seb::mbar_wait_bounded(tbar, 0, 1 << 20);
+    }
+  }
+  if (tid == 0 && staged) {
     const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
     const uint32_t a_lbo = (uint32_t)T.S * 16u, b_lbo = (kHid / 8) * 128;
     for (int m = 0; m < T.mt; ++m) {
@@ -709,11 +731,12 @@ __global__ void __launch_bounds__(kTcM, 2) conv_tc_tile_kernel(const bf16* __res
             "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(acc));
       }
     }
-    sync.commit();
   }
-  if (!sync.wait(0)) {
-    // the MMAs did not finish in time: report it, give them one more bounded wait (they write
-    // this CTA's tensor memory) and leave the tile unwritten
+  if (tid == 0) sync.commit();  // (with no MMA issued, the commit still completes the phase)
+  const bool mma_done = sync.wait(0);
+  if (!__syncthreads_and(mma_done && staged)) {
+    // the copy or the MMAs did not finish in time: report it, give the MMAs one more bounded
+    // wait (they write this CTA's tensor memory) and leave the tile unwritten
     if (tid == 0) {
       atomicOr(err, 4u);
       sync.wait(0);
@@ -794,7 +817,8 @@ __global__ void transpose_w_kernel(const bf16* __restrict__ w, bf16* __restrict_
 // tap (u, v) of GEMM row m = r Pt + c reads staged pixel m + (2 - u) d Pt + (2 - v) d.  The window
 // is staged twice, the hi then the lo half of the split gradient, into the same shared memory;
 // the lo MMAs accumulate onto the hi ones.
-__global__ void __launch_bounds__(kTcM, 2) conv_bwd_dx_tile_kernel(const bf16* __restrict__ dzs,
+__global__ void __launch_bounds__(kTcM, 2) conv_bwd_dx_tile_kernel(const __grid_constant__ CUtensorMap zmap,
+                                                                   int use_map, const bf16* __restrict__ dzs,
                                                                    const bf16* __restrict__ wt, int H, int W, int d,
                                                                    ConvTile T, int tiles_x, int tiles_y,
                                                                    float* __restrict__ dx, uint32_t* err) {
@@ -803,6 +827,7 @@ __global__ void __launch_bounds__(kTcM, 2) conv_bwd_dx_tile_kernel(const bf16* _
   uint8_t* Bs = tsm + kCtBOff;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(tsm + kCtBarOff);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(tsm + kCtBarOff + 16);
+  uint64_t* tbar = reinterpret_cast<uint64_t*>(tsm + kCtBarOff + 32);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int Ho = H - 2 * d, Wo = W - 2 * d;
   if (blockDim.x != kTcM || T.S > kCtMaxS || T.mt < 1 || T.mt > 4) {
@@ -820,24 +845,43 @@ __global__ void __launch_bounds__(kTcM, 2) conv_bwd_dx_tile_kernel(const bf16* _
     *reinterpret_cast<uint4*>(Bs + tc_off(c, kc * 8, kHid / 8)) =
         reinterpret_cast<const uint4*>(wt + (int64_t)c * kTcK)[kc];
   }
-  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
+    if (use_map) seb::mbar_init(tbar, 1);
+  }
   const uint32_t tmem = tmem_alloc_cols(tslot, warp, 128);
   const TcSync sync{mbar};
-  const int rows = T.R + 2 * d;
   bool ok = true;
   for (int part = 0; part < 2 && ok; ++part) {  // 0: hi, 1: lo
-    for (int e = tid; e < T.S * 4; e += kTcM) {
-      const int s = e >> 2, g = e & 3;
-      const int rr = s / T.Pt, cc = s - rr * T.Pt;
-      const int gi = i0 - 2 * d + rr, gj = j0 - 2 * d + cc;
-      const bool in = rr < rows && gi >= 0 && gi < Ho && gj >= 0 && gj < Wo;
-      const bf16* src = in ? dzs + (((int64_t)b * Ho + gi) * Wo + gj) * 2 * kHid + part * kHid + g * 8 : dzs;
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(As + ((size_t)g * T.S + s) * 16)),
-                   "l"(src), "r"(in ? 16u : 0u)
-                   : "memory");
+    if (use_map) {
+      // four TMA boxes of the window (channel groups of the hi or the lo half of the split
+      // gradient), waited for by the thread that issues the MMAs
+      if (tid == 0) {
+        seb::mbar_arrive_expect_tx(tbar, (uint32_t)(T.Pt * (T.R + 2 * d)) * 64u);
+        for (int g = 0; g < 4; ++g)
+          seb::tma_load_4d(As + (size_t)g * T.S * 16, &zmap, kHid * part + 8 * g, j0 - 2 * d, i0 - 2 * d, b, tbar);
+        if (!seb::mbar_wait_bounded(tbar, (uint32_t)part, 1 << 20)) {
+          atomicOr(err, 8u);
+          seb::mbar_wait_bounded(tbar, (uint32_t)part, 1 << 20);
+          ok = false;
+        }
+      }
+      ok = __syncthreads_and(ok) != 0;
+      if (!ok) break;
+    } else {
+      for (int e = tid; e < T.S * 4; e += kTcM) {
+        const int s = e >> 2, g = e & 3;
+        const int rr = s / T.Pt, cc = s - rr * T.Pt;
+        const int gi = i0 - 2 * d + rr, gj = j0 - 2 * d + cc;
+        const bool in = gi >= 0 && gi < Ho && gj >= 0 && gj < Wo;
+        const bf16* src = in ? dzs + (((int64_t)b * Ho + gi) * Wo + gj) * 2 * kHid + part * kHid + g * 8 : dzs;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(As + ((size_t)g * T.S + s) * 16)),
+                     "l"(src), "r"(in ? 16u : 0u)
+                     : "memory");
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands visible to the tensor core
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -1403,18 +1447,40 @@ static ConvTile conv_tile(int d, int Ho, int Wo) {
     const int C = c < Wo ? c : Wo;
     const int Pt = C + 2 * d;
     int R = (4 * kTcM) / Pt < Ho ? (4 * kTcM) / Pt : Ho;
-    auto staged = [&](int r) { return (r * Pt + kTcM - 1) / kTcM * kTcM + 2 * d * Pt + 2 * d; };
-    while (R > 0 && staged(R) > kCtMaxS) --R;
+    // window pixels per channel group, and one past the last pixel a GEMM row of the M tiles
+    // reads (rows past the tile read on into the next group's window, or past the last one)
+    auto win = [&](int r) { return (Pt * (r + 2 * d) + 7) / 8 * 8; };
+    auto reach = [&](int r) { return (r * Pt + kTcM - 1) / kTcM * kTcM + 2 * d * Pt + 2 * d; };
+    while (R > 0 && (win(R) > kCtMaxS || 3 * win(R) + reach(R) > 4 * kCtMaxS)) --R;
     if (R > 0) {
-      const double score = (double)((Wo + C - 1) / C) * ((Ho + R - 1) / R) * staged(R);
+      const double score = (double)((Wo + C - 1) / C) * ((Ho + R - 1) / R) * win(R);
       if (score < best_score) {
         best_score = score;
-        best = ConvTile{C, R, Pt, (R * Pt + kTcM - 1) / kTcM, staged(R)};
+        best = ConvTile{C, R, Pt, (R * Pt + kTcM - 1) / kTcM, win(R)};
       }
     }
     if (C == Wo) break;
   }
   return best;
+}
+
+// 4-D tensor map of a [B][H][W][chans] BF16 buffer whose box {8 channels, Pt columns, rows,
+// 1 image} lands in shared memory as [pixel][16 bytes] (zero outside the image); the kernels load
+// one box per channel group g (first coordinate 8 g) to build the [group][pixel][16 bytes] window.
+// False (the kernels then stage with cp.async) when the driver's encoder is missing or the buffer
+// or the box does not meet TMA's rules.
+static bool window_map(CUtensorMap* m, const bf16* base, int B, int H, int W, int chans, int Pt, int rows) {
+  memset(m, 0, sizeof(*m));
+  PFN_cuTensorMapEncodeTiled_v12000 enc = seb::tensor_map_encoder();
+  if (!enc || ((uintptr_t)base & 15) != 0 || Pt > 256 || rows > 256) return false;
+  const cuuint64_t px = (cuuint64_t)chans * 2;  // bytes per pixel
+  const cuuint64_t dims[4] = {(cuuint64_t)chans, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {px, px * W, px * W * H};
+  const cuuint32_t box[4] = {8, (cuuint32_t)Pt, (cuuint32_t)rows, 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // One 3x3 layer l (0..3) on x [B][S][S'][Cin] -> y; the 32 -> 32 layers use the tensor-core
@@ -1430,9 +1496,11 @@ static void conv_layer(seb_sur* h, const bf16* x, int l, int B, int H, int W, bf
     const int d = kDil[l], Ho = H - 2 * d, Wo = W - 2 * d;
     const ConvTile T = conv_tile(d, Ho, Wo);
     const int tx = (Wo + T.C - 1) / T.C, ty = (Ho + T.R - 1) / T.R;
+    CUtensorMap xm;
+    const int use_map = window_map(&xm, x, B, H, W, kHid, T.Pt, T.R + 2 * d) ? 1 : 0;
     cudaFuncSetAttribute(conv_tc_tile_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCtSmem);
     conv_tc_tile_kernel<true><<<(unsigned)((int64_t)B * ty * tx), kTcM, kCtSmem, h->stream>>>(
-        x, wb + h->PL.w[l], master + h->PL.b[l], H, W, d, T, tx, ty, y, h->err);
+        xm, use_map, x, wb + h->PL.w[l], master + h->PL.b[l], H, W, d, T, tx, ty, y, h->err);
   } else {
     conv_fwd_kernel<kHid><<<grid_for(pix, 128), 128, 0, h->stream>>>(x, wb + h->PL.w[l], master + h->PL.b[l], B, H,
                                                                       W, kDil[l], y);
@@ -1523,9 +1591,11 @@ int seb_sur_train_step(seb_sur* h, int32_t B, float lr, int32_t step, float* los
       transpose_w_kernel<<<grid_for(kHid * kTcK, 256), 256, 0, st>>>(wb + h->PL.w[l], wt);
       const ConvTile T = conv_tile(d, S, S);
       const int tx = (S + T.C - 1) / T.C, ty = (S + T.R - 1) / T.R;
+      CUtensorMap zm;
+      const int use_map = window_map(&zm, dzs, B, S - 2 * d, S - 2 * d, 2 * kHid, T.Pt, T.R + 2 * d) ? 1 : 0;
       cudaFuncSetAttribute(conv_bwd_dx_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCtSmem);
       conv_bwd_dx_tile_kernel<<<(unsigned)((int64_t)B * ty * tx), kTcM, kCtSmem, st>>>(
-          dzs, wt, S, S, d, T, tx, ty, at<float>(h, h->v.dact[l - 1]), h->err);
+          zm, use_map, dzs, wt, S, S, d, T, tx, ty, at<float>(h, h->v.dact[l - 1]), h->err);
     } else {
       const int E = kHid * 9 * kHid + kHid;
       conv_bwd_dw_kernel<kHid><<<ch, 256, 0, st>>>(dy, y, xin, B, S, S, d, part);
