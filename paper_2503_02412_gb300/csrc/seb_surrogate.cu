@@ -522,9 +522,6 @@ __global__ void init_kernel(float* __restrict__ p, float* __restrict__ m, float*
 constexpr int kTcM = 128;
 constexpr int kTcK = 9 * kHid;                      // 288
 constexpr int kTcKCores = kTcK / 8;                  // 36
-constexpr int kTcBOff = 72 * 1024;                   // B right after A (128 x 288 BF16), 1 KB aligned
-constexpr int kTcBarOff = kTcBOff + 18 * 1024;       // after B (32 x 288 BF16)
-static_assert(kTcBOff >= kTcM * kTcK * 2 && kTcBarOff >= kTcBOff + kHid * kTcK * 2, "operand regions overlap");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
