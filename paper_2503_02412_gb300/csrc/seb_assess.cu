@@ -970,11 +970,18 @@ __global__ void copy_out_kernel(const Launch L, float* __restrict__ dst, uint8_t
 
 // Tiling of the requested rectangles for assess_kernel (v2 layouts, tiles start at the
 // rectangle's corner).
-void decompose_v2(Launch& L) {
+// Both tilings return false if the rectangles would not fit Launch::rects (not reached with the
+// at most 4 requested rectangles and 3 rectangles per request; checked all the same).
+bool decompose_v2(Launch& L) {
   L.n_rects = 0;
   L.tile_start[0] = 0;
+  bool fits = true;
   auto push = [&](int x0, int y0, int w, int h, int lg) {
     if (w <= 0 || h <= 0) return;
+    if (L.n_rects >= kMaxRects) {
+      fits = false;
+      return;
+    }
     const int i = L.n_rects++;
     L.rects[i] = Rect{x0, y0, w, h, x0, y0, lg};
     const int tw = kG << lg, th = kThreads >> lg;
@@ -994,16 +1001,22 @@ void decompose_v2(Launch& L) {
       push(q.x0, q.y0, q.w, q.h, 5);
     }
   }
+  return fits;
 }
 
 // Tiling for assess_kernel_sl: tile grids start on globally aligned blocks (column = 0 mod 4,
 // row = 0 mod 2 in global cells), so a rectangle's grid may start up to 3 columns / 1 row
 // before it; those cells are computed but not stored.
-void decompose_sl(Launch& L) {
+bool decompose_sl(Launch& L) {
   L.n_rects = 0;
   L.tile_start[0] = 0;
+  bool fits = true;
   auto push = [&](int tx, int ty, int sx0, int sy0, int sx1, int sy1, int lay) {
     if (sx1 <= sx0 || sy1 <= sy0) return;
+    if (L.n_rects >= kMaxRects) {
+      fits = false;
+      return;
+    }
     const int i = L.n_rects++;
     L.rects[i] = Rect{sx0, sy0, sx1 - sx0, sy1 - sy0, tx, ty, lay};
     const int tw = sl_tw(lay), th = sl_th(lay);
@@ -1042,6 +1055,7 @@ void decompose_sl(Launch& L) {
       push(ax, ay, q.x0, q.y0, x1, y1, 5);
     }
   }
+  return fits;
 }
 
 size_t pairs_sl(const Tables& T, const Launch& L) {
@@ -1134,7 +1148,7 @@ template <typename E, bool COMP>
 cudaError_t launch_typed(const Tables& T, const Launch& Lreq, cudaStream_t stream) {
   Launch L = Lreq;
   {
-    decompose_sl(L);
+    if (!decompose_sl(L)) return cudaErrorInvalidValue;
     // 16-byte stores of whole cell blocks need 4 | nx (no ring wrap inside a block) and
     // aligned output planes
     L.vec4 = (L.nx % 4 == 0) && ((uintptr_t)L.out % 16 == 0) && ((uintptr_t)L.flags % 4 == 0);
@@ -1153,7 +1167,7 @@ cudaError_t launch_typed(const Tables& T, const Launch& Lreq, cudaStream_t strea
     }
     // very large footprints: the per-cell kernel below
   }
-  decompose_v2(L);
+  if (!decompose_v2(L)) return cudaErrorInvalidValue;
   if (L.tile_start[L.n_rects] == 0) return cudaSuccess;
   size_t smem = 0;
   for (int i = 0; i < L.n_rects; ++i) {
