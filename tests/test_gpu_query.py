@@ -267,3 +267,49 @@ def test_one_pose_per_thread_kernels(seb, side):
     abi.seb_query_poses_backward(p, te.data_ptr(), 0, 0, tp.data_ptr(), sv.data_ptr(), go.data_ptr(), a.data_ptr(), n, st)
     abi.seb_query_poses_backward(p, te.data_ptr(), 0, 0, tp.data_ptr(), 0, go.data_ptr(), b.data_ptr(), n, st)
     assert torch.allclose(a, b, rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("dtype,side,n", [(torch.bfloat16, 100, 4096), (torch.bfloat16, 180, 70_000),
+                                          (torch.float16, 100, 70_000), (torch.float16, 180, 4096)])
+def test_reduced_precision_windows(seb, dtype, side, n):
+    """BF16 / FP16 windows: the query widens each corner height to FP32, so it matches the FP64
+    oracle run on the stored (rounded) heights.  4,096 poses take the grouped kernels, 70,000 the
+    one-pose-per-thread kernels (a 100 x 100 or 180 x 180 window of 2-byte heights, 20 or 65 KB,
+    is copied into shared memory)."""
+    from paper_2503_02412_gb300.query import query_poses
+
+    cfg = dict(C1, nx=side, ny=side)
+    p = seb.SebParams(**cfg, elev_dtype=dtype)
+    te = torch.from_numpy(bumpy_plane(21, side, side)).cuda().to(dtype)
+    stored = te.float().cpu().numpy().astype(np.float64)
+    poses = random_poses(22, n, side, side, 0.1, 5)
+    out, fl = query_poses(p, te, torch.from_numpy(poses).cuda())
+    idx = np.random.default_rng(23).integers(0, n, min(n, 3000))
+    r, rf = oracle.query_poses(oracle.OracleParams(**cfg), stored, poses[idx].astype(np.float64))
+    s = compare(out.cpu().numpy()[idx], fl.cpu().numpy()[idx], r, rf, label=f"{dtype} query")
+    assert s["assessed"] > 0.5 * len(idx)
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+def test_reduced_precision_backward(seb, dtype):
+    """The adjoint on a BF16 / FP16 window (70,000 poses: the one-pose-per-thread kernels with the
+    window in shared memory) against the FP64 oracle adjoint on the stored heights."""
+    from paper_2503_02412_gb300.query import QueryPoses
+
+    cfg = dict(C1, kappa_max=1.0, phi_x_max=1.4, phi_y_max=1.4)
+    p = seb.SebParams(**cfg, elev_dtype=dtype)
+    te = torch.from_numpy(bumpy_plane(24)).cuda().to(dtype)
+    stored = te.float().cpu().numpy().astype(np.float64)
+    n = 70_000
+    poses = random_poses(25, n, 100, 100, 0.1, 5)
+    gout = np.random.default_rng(26).normal(size=(n, 5))
+    tp = torch.from_numpy(poses).cuda().requires_grad_(True)
+    out, fl = QueryPoses.apply(tp, te, p, (0, 0))
+    (out * torch.from_numpy(gout).float().cuda()).sum().backward()
+    g, fl = tp.grad.cpu().numpy(), fl.cpu().numpy()
+    idx = np.random.default_rng(27).integers(0, n, 2000)
+    r = oracle.query_poses_vjp(oracle.OracleParams(**cfg), stored, poses[idx].astype(np.float64), gout[idx])
+    sel = (fl[idx] & 5) == 0
+    assert sel.mean() > 0.8
+    sc = np.abs(r[sel]).max(axis=0)
+    assert (np.abs(g[idx] - r)[sel] / sc).max() < 1e-3
