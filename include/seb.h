@@ -444,7 +444,8 @@ int seb_sur_forward(seb_sur* h, int32_t batch);
  * map (roughness is not predicted: NaN, flag SEB_FLAG_SURROGATE) for the cells at least 16
  * from the border; mask_dev [ny][nx] (may be NULL) receives the fallback mask (a NaN or a
  * 4-neighbour step above `step` metres within Chebyshev distance `radius`, or the border);
- * with exact_fallback != 0 the exact kernel then overwrites every masked cell.
+ * with exact_fallback != 0 the exact kernel then overwrites every masked cell (border cells
+ * included); with exact_fallback == 0 the border cells of out_dev and flags_dev are not written.
  */
 int seb_sur_infer(seb_sur* h, const float* elev_dev, float step, int32_t radius, int32_t exact_fallback,
                   float* out_dev, uint8_t* flags_dev, uint8_t* mask_dev);

@@ -143,6 +143,31 @@ def test_map_inference_equals_batch_path(mods, engine):
     assert ((fl[:, 16:80, 16:80] & seb.abi.SEB_FLAG_SURROGATE) != 0).all()
 
 
+def test_engines_agree_on_a_non_square_map(mods):
+    """Map inference of a 120 x 88 window with the tcgen05 engine (2-D tiles of the feature map,
+    ragged at the right and bottom edges) and with the CUDA-core engine: the same network, so the
+    predictions agree to BF16 rounding of the activations (a few BF16 ulps after four layers)."""
+    seb, surrogate = mods
+    s = surrogate.Surrogate(seb.SebParams(nx=120, ny=88, **C2), max_batch=1)
+    s.init(11)
+    e = torch.from_numpy(bumpy_plane(12, 120, 88, 0.05)).cuda()
+    s.set_engine("tcgen05")
+    a, fa, ma = s.infer(e, exact_fallback=False)
+    a = a.clone()
+    s.set_engine("simt")
+    b, fb, mb = s.infer(e, exact_fallback=False)
+    # without the exact fallback only the cells at least 16 from the border are written
+    a, b, fa, fb = a[..., 16:72, 16:104], b[..., 16:72, 16:104], fa[..., 16:72, 16:104], fb[..., 16:72, 16:104]
+    assert torch.equal(fa, fb) and torch.equal(ma, mb)
+    assert ((fa & seb.abi.SEB_FLAG_SURROGATE) != 0).all()
+    sel = torch.isfinite(a) & torch.isfinite(b)
+    assert sel.float().mean() > 0.5
+    d = (a - b)[sel].abs()
+    scale = b[sel].abs().max()
+    assert float(d.max()) <= 0.05 * float(scale), (float(d.max()), float(scale))
+    assert float(d.mean()) <= 0.005 * float(scale)
+
+
 def test_exact_fallback_cells(mods):
     seb, _ = mods
     s = make(mods, nx=160, batch=1, seed=9)
