@@ -781,7 +781,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       // qxx = (hi + 1)^2 X1 - 2 (hi + 1) X2 + 2 X3 - X2.
       float2 Ab = zero2, Tb = zero2, Cb = zero2;
       int k1 = 0, k2 = 0, k3 = 0;
-#pragma unroll 2
+#pragma unroll 4
       for (int k = 0; k < len; ++k) {
         const float2 v = pq[k];
         const uint32_t mx = 0u - (uint32_t)(v.x == v.x), my = 0u - (uint32_t)(v.y == v.y);
