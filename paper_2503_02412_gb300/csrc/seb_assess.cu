@@ -1,20 +1,22 @@
-// SE(2)-grid traversability assessment kernel (Algorithm 1 of Sec. V-B for every cell and
+// SE(2)-grid traversability assessment kernels (Algorithm 1 of Sec. V-B for every cell and
 // yaw bin), plus the ring-unrolling copy.
 //
-// One CTA = one 32 x 32 tile of cells x one yaw pair {k, k + K/2} (the two bins share a
-// footprint, so their moments, normal and roughness are computed once; pitch and roll
-// change sign).  The tile and its footprint halo are staged in shared memory as FP32
-// (cells outside the window read as NaN = unknown, Sec. V-A).  Each thread owns 4
-// adjacent cells of one row and walks the yaw's row runs with a 4-wide register window,
-// so one shared-memory load feeds 4 cells.
+// Two kernels share the finish (finish_cell).  Both run one CTA per tile of cells and yaw pair
+// {k, k + K/2}: the two bins share a footprint, so their moments, normal and roughness are
+// computed once, and pitch and roll change sign.  The tile and its footprint halo are staged in
+// shared memory (cells outside the window read as NaN = unknown, Sec. V-A).
+//   - assess_kernel_sl (every footprint whose staged tile fits): cells in world-aligned blocks of
+//     4 columns x 2 rows, one block per thread, sliding row sums on packed FP32 pairs, the tile
+//     staged by one TMA copy; see the block comment above the kernel.
+//   - assess_kernel (very large footprints): each thread owns 4 adjacent cells of one row and walks
+//     the yaw's row runs with a 4-wide register window, so one shared-memory load feeds 4 cells.
 //
-// Moments are accumulated about a per-cell reference height (the cell's own elevation,
-// or the first known footprint cell in run order when the centre is unknown):
-//   S0 = sum z', S1 = sum di z', S2 = sum dj z', S3 = sum z'^2,  z' = z - ref,
-// with dj folded per run.  The xy moments (N, sum di, ..., sum dj^2) are exact integers:
-// the table's when the tile has no unknown cell, else summed from the known mask.  Every
-// cell's arithmetic therefore depends on its neighbourhood only, never on the tile
-// position, which makes the rolling update bit-identical to a full rebuild.
+// Moments are accumulated about a reference height (the sliding kernel: one per block, the
+// per-cell kernel: the cell's own elevation, or the first known footprint cell in run order when
+// the centre is unknown): S0 = sum z', S1 = sum di z', S2 = sum dj z', S3 = sum z'^2, z' = z - ref.
+// The xy moments (N, sum di, ..., sum dj^2) are exact integers: the table's minus those of the
+// missing points.  Every cell's arithmetic therefore depends on its neighbourhood only, never on
+// the tile position, which makes the rolling update bit-identical to a full rebuild.
 //
 // Covariance (population, /N, Algorithm 1) from the moments; smallest eigenpair by the
 // trigonometric closed form for symmetric 3x3 matrices (O. K. Smith, "Eigenvalues of a
