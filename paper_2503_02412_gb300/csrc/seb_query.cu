@@ -390,6 +390,7 @@ __device__ __forceinline__ bool lattice_point(const QTab& Q, const QLaunch& L, i
 // forward stream and the adjoint stream; measured on 1 M poses: the adjoint's larger state
 // leaves room for 2).
 constexpr int kQB = 4, kQBB = 2;
+constexpr int kQBS = 2;  // the same for the forward with the window in shared memory (lower latency)
 
 // Moments of one pose by one thread, streaming its lattice in order (sums centred on the first
 // known point, as the grouped kernels do, but added in lattice order).
@@ -433,12 +434,12 @@ __device__ __forceinline__ void stream_moments(const QTab& Q, const QLaunch& L, 
 // One pose per thread, for large batches: a warp then runs the eigen-solve, frame and adjoint
 // for 32 poses per pass (a group of GL lanes per pose runs them for 32 / GL).  `elev` is the
 // window in global memory, or its copy in the CTA's shared memory.
-template <typename E>
+template <typename E, int QB = kQB>
 __device__ __forceinline__ void fwd1_pose(const QTab& Q, const QLaunch& L, const E* __restrict__ elev, int64_t i) {
   float xl, yl, c, s;
   pose_local(L, L.poses + 3 * i, xl, yl, c, s);
   float m[10], zref;
-  stream_moments<E, kQB>(Q, L, elev, xl, yl, c, s, m, zref);
+  stream_moments<E, QB>(Q, L, elev, xl, yl, c, s, m, zref);
   QState S;
   finish_pose(Q, L, m, zref, c, s, S);
   store_pose(L, i, S);
@@ -534,7 +535,7 @@ __global__ void __launch_bounds__(256, 3) query1_smem_kernel(const __grid_consta
     if (BWD)
       bwd1_pose<E>(Q, L, map, i);
     else
-      fwd1_pose<E>(Q, L, map, i);
+      fwd1_pose<E, kQBS>(Q, L, map, i);
   }
 }
 
